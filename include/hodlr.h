@@ -1,0 +1,202 @@
+/*
+ * hodlr.h -- C ABI of the GB300 (sm_103a) adaptive-precision HODLR library.
+ *
+ * The method is that of Carson, Chen and Liu, "Mixed Precision HODLR
+ * Matrices" (arXiv 2407.21637).  A HODLR matrix on the cluster tree of
+ * Def. 2.1 stores, for every level k = 1..depth and every sibling pair of
+ * nodes (i, i^1), the low-rank generators of the off-diagonal block
+ * H(I_i, I_{i^1}) ~ U_i V_{i^1}^T (eq. (2.1), eq. (3.1)), and the dense leaf
+ * blocks D_i.  Algorithm 3.2 stores each generator in the precision its
+ * level (or block) admits; Algorithm 3.3 multiplies by the result.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Indices are in tree order: the caller has already permuted its points.
+ * - Tree: the root is {0..n-1}; a node of size m splits into a left child of
+ *   size ceil(m/2) and a right child of size m - ceil(m/2) (the practical
+ *   split of Sect. 4).  Level k has 2^k nodes numbered i = 0..2^k-1 from
+ *   left to right; the sibling of node i is i^1.
+ * - Node tables ("per node") list the nodes of level 1, then level 2, ...,
+ *   then level depth: 2^(depth+1) - 2 entries; node (k, i) is entry
+ *   2^k - 2 + i.
+ * - Matrices passed as host arrays are fp64, row-major, dense.
+ * - X and B of a product are DEVICE arrays, row-major (n, nrhs) with a
+ *   leading dimension in elements; the right-hand sides are the fastest
+ *   index.  They are owned by the caller.  The library owns the handle and
+ *   every byte it allocates; hodlr_destroy frees them.
+ * - Every call that launches GPU work takes a CUDA stream (cudaStream_t
+ *   passed as void*; NULL = legacy default stream), enqueues on it and
+ *   returns without waiting unless stated otherwise.
+ * - Errors are returned as hodlr_status.  Arguments are validated before
+ *   anything is launched; nothing aborts or exits, and there is no CPU
+ *   fallback: a call that cannot run on the GPU returns an error.
+ * - A handle may be used from one host thread at a time.
+ */
+#ifndef HODLR_H
+#define HODLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hodlr_s* hodlr_t;
+
+typedef enum {
+  HODLR_OK = 0,
+  HODLR_EINVAL = 1,       /* bad argument (null pointer, size, rank, stride, precision) */
+  HODLR_ENOMEM = 2,       /* device or host allocation failed */
+  HODLR_ECUDA = 3,        /* a CUDA runtime call failed */
+  HODLR_ETIMEOUT = 4,     /* a device-side bounded wait gave up */
+  HODLR_ENOTFACTORED = 5, /* solve before factorisation */
+  HODLR_ESINGULAR = 6,    /* zero pivot */
+  HODLR_EACCURACY = 7     /* a requested tolerance could not be met */
+} hodlr_status;
+
+/* Storage / arithmetic formats (Table 1.1; E5M2 is the paper's q52, E4M3 is
+ * the OCP FP8 "fn" format).  The value is the bit index used in tier_mask. */
+typedef enum {
+  HODLR_FP64 = 0,
+  HODLR_FP32 = 1,
+  HODLR_FP16 = 2,
+  HODLR_BF16 = 3,
+  HODLR_E4M3 = 4,
+  HODLR_E5M2 = 5
+} hodlr_prec;
+
+/* Options of the adaptive-precision format (Algorithm 3.2 inputs). */
+typedef struct {
+  double eps;          /* truncation parameter epsilon of Def. 2.3 (0 < eps < 1) */
+  int32_t work;        /* working precision u: HODLR_FP64 or HODLR_FP32.  The leaves
+                          are stored in it and the products are computed in it
+                          (Algorithm 3.2 step "store in u", Algorithm 3.3). */
+  uint32_t tier_mask;  /* the set calU of available storage formats: bit p set for
+                          hodlr_prec p.  The working precision is always added. */
+  int32_t per_block;   /* 0: xi_k = max over the level (Algorithm 3.2 as printed);
+                          1: xi_ij per block (same Thm 3.1 bound) */
+  int32_t max_nrhs;    /* widest product one launch sequence handles (scratch size);
+                          wider products are split into column batches.  0 -> 64 */
+} hodlr_opts;
+
+/* Summary of a stored HODLR matrix.  Arrays are indexed by level k = 1..depth
+ * (entry 0 unused); depth <= HODLR_MAX_DEPTH. */
+#define HODLR_MAX_DEPTH 24
+typedef struct {
+  int32_t n, depth, work, per_block;
+  int32_t max_rank;                 /* largest off-diagonal rank */
+  int32_t n_blocks;                 /* 2^(depth+1) - 2 off-diagonal blocks */
+  int64_t factor_bytes;             /* algorithmic bytes of U and V (no padding) */
+  int64_t leaf_bytes;               /* algorithmic bytes of the leaves */
+  int64_t scale_bytes;              /* 8 bytes per block with a power-of-two scale */
+  int64_t device_bytes;             /* bytes the handle holds on the device */
+  int64_t bytes_per_tier[6];        /* factor bytes per hodlr_prec */
+  double norm2_all;                 /* ||H||_F^2 estimate used for xi (from the factors) */
+  double xi[HODLR_MAX_DEPTH + 1];   /* xi_k (per_block: the level maximum of xi_ij) */
+  double u_prime[HODLR_MAX_DEPTH + 1]; /* u'_k = eps / (2^{k/2} xi_k) */
+  int32_t level_tier[HODLR_MAX_DEPTH + 1]; /* u_k as hodlr_prec (per_block: most precise
+                                              tier used on the level) */
+} hodlr_info_t;
+
+/* ---------------------------------------------------------------------- */
+/* hodlr_import -- store given fp64 generators in the adaptive-precision
+ * format (Algorithm 3.2, steps after the compression).
+ *
+ *  n, depth      matrix size and tree depth; 1 <= 2^depth <= n, depth <= 24.
+ *  ranks         host, per node: ranks[node(k,i)] = rank of block (i, i^1).
+ *  U             host, per node: U[node(k,i)] -> m_i x ranks[node(k,i)] fp64,
+ *                row-major; the left generator of block (i, i^1), with
+ *                orthonormal columns (eq. (3.1)).  May be NULL when the rank is 0.
+ *  V             host, per node: V[node(k,j)] -> m_j x ranks[node(k,j^1)] fp64,
+ *                row-major; the right generator of block (j^1, j), so that
+ *                H(I_{j^1}, I_j) ~ U[node(k,j^1)] V[node(k,j)]^T.
+ *  D             host, per leaf i = 0..2^depth-1: m_i x m_i fp64 row-major.
+ *  opts          see hodlr_opts.
+ *  stream        work is enqueued here; the call synchronises this stream
+ *                before returning (it reads the block norms back).
+ *  out           receives the new handle (unchanged on error).
+ *
+ * The precision of every block is chosen on the device-computed norms of the
+ * fp64 generators: ||U_i V_{i^1}^T||_F = ||V_{i^1}||_F because U_i has
+ * orthonormal columns, and ||H||_F^2 is estimated by the sum of the block
+ * norms plus the leaves' (the O(eps) estimate allowed in Sect. 3.2).
+ * u'_k = eps / (2^{k/2} xi_k); u_k = the largest available u* <= u'_k, or the
+ * most precise available format when none qualifies.  fp16/E4M3/E5M2
+ * generators carry a per-block power-of-two scale s = 2^floor(log2(x_max /
+ * (2 amax))); rounding is to nearest, ties to even.
+ * Errors: HODLR_EINVAL for bad sizes/ranks/precisions, HODLR_ENOMEM,
+ * HODLR_ECUDA. */
+hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks,
+                          const double* const* U, const double* const* V,
+                          const double* const* D, const hodlr_opts* opts,
+                          void* stream, hodlr_t* out);
+
+/* hodlr_export -- read the stored generators back, decoded to fp64 (the
+ * values Algorithm 3.3 multiplies by: stored / scale).  Same layouts as
+ * hodlr_import; any of U, V, D may be NULL to skip it.  Synchronous. */
+hodlr_status hodlr_export(hodlr_t h, double* const* U, double* const* V,
+                          double* const* D, void* stream);
+
+/* hodlr_matvec -- B = H-hat X by Algorithm 3.3 (HODLR_MATVEC), all levels
+ * and the leaves, for nrhs right-hand sides.
+ *
+ *  X       device, (n, nrhs) row-major, leading dimension ldx >= nrhs,
+ *          element type = the working precision (double for HODLR_FP64,
+ *          float for HODLR_FP32).
+ *  B       device, (n, nrhs) row-major, ldb >= nrhs, same type; overwritten.
+ *          B must not overlap X.
+ *  xb_prec the element type of X and B; must equal the handle's working
+ *          precision (HODLR_EINVAL otherwise).
+ * Low-precision generators are cast to the working precision as they are
+ * loaded (Sect. 3.3); every product and sum is in the working precision.
+ * Each output entry is written exactly once, by a fixed summation order, so
+ * results are bitwise reproducible run to run.  nrhs = 0 is a no-op.
+ * Calls on one handle must not overlap in time (they share its scratch);
+ * enqueue them on one stream.  Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
+                          void* B, int64_t ldb, int32_t xb_prec, void* stream);
+
+/* hodlr_info -- sizes, bytes per tier and the precision rule's quantities. */
+hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out);
+
+/* hodlr_block_tiers -- per node (layout as ranks in hodlr_import): the storage
+ * format (hodlr_prec) and rank of block (i, i^1).  Either output may be NULL. */
+hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks);
+
+/* hodlr_dense_kernel_matvec -- on-the-fly FP64 dense product b = A x for a
+ * kernel matrix A_ij = f(x_i, x_j) + diag * delta_ij, used to check HODLR
+ * products at sizes where A cannot be stored (its entries are generated in
+ * registers, never stored).  Kinds: 0 1/(r+c), 1 exp(-r^2/len2), 2 log(r+c),
+ * 3 1/(x_i - x_j) (1D) -- the test kernels of eq. (4.1) and the synthetic
+ * workloads; at i == j, f is f(0) where finite and 0 otherwise.
+ *
+ *  points  device, (n, dim) fp64 row-major, dim in {1, 2, 3}.
+ *  rows    device int32[nrows]: the rows of A to compute (any subset, any
+ *          order); NULL means all n rows in order (nrows must equal n).
+ *          An entry outside [0, n) gives a row of NaN.
+ *  X       device fp64 (n, nrhs) row-major, ldx >= nrhs.
+ *  B       device fp64 (nrows, nrhs) row-major, ldb >= nrhs; overwritten.
+ * Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_dense_kernel_matvec(int32_t n, int32_t dim, const double* points,
+                                       int32_t kind, double c, double len2, double diag,
+                                       int32_t nrows, const int32_t* rows,
+                                       int32_t nrhs, const double* X, int64_t ldx,
+                                       double* B, int64_t ldb, void* stream);
+
+/* hodlr_destroy -- free the handle and its device memory (synchronises the
+ * device work the handle owns).  NULL is a no-op. */
+void hodlr_destroy(hodlr_t h);
+
+/* hodlr_status_string -- static, human-readable text of a status code. */
+const char* hodlr_status_string(hodlr_status s);
+
+/* hodlr_last_error -- text of the last error on this host thread (e.g. the
+ * CUDA error string or which argument was invalid); static storage. */
+const char* hodlr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HODLR_H */

@@ -1,0 +1,557 @@
+// C ABI of libhodlr: handle management, validation, the precision rule of
+// Algorithm 3.2 (on device-computed norms), layout planning and launches.
+#include <algorithm>
+#include <cmath>
+#include <memory>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hodlr_internal.cuh"
+
+using namespace hodlr;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hodlr_status fail(hodlr_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+hodlr_status cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return HODLR_ECUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+double unit_roundoff(int p) {
+  switch (p) {
+    case HODLR_FP64: return std::ldexp(1.0, -53);
+    case HODLR_FP32: return std::ldexp(1.0, -24);
+    case HODLR_FP16: return std::ldexp(1.0, -11);
+    case HODLR_BF16: return std::ldexp(1.0, -8);
+    case HODLR_E4M3: return std::ldexp(1.0, -4);
+    case HODLR_E5M2: return std::ldexp(1.0, -3);
+  }
+  return 1.0;
+}
+
+// Largest finite value of the formats that get a per-block scale.
+double scaled_format_max(int p) {
+  switch (p) {
+    case HODLR_FP16: return 65504.0;
+    case HODLR_E4M3: return 448.0;
+    case HODLR_E5M2: return 57344.0;
+  }
+  return 0.0;
+}
+
+// s = 2^floor(log2(x_max / (2 amax))) for fp16/e4m3/e5m2, else 1.
+double pow2_scale(double amax, int p) {
+  const double xm = scaled_format_max(p);
+  if (xm == 0.0 || amax == 0.0) return 1.0;
+  int e = 0;
+  std::frexp(xm / (2.0 * amax), &e);  // y = f 2^e, f in [0.5, 1)
+  return std::ldexp(1.0, e - 1);
+}
+
+// u_k = max{u* <= u' : u* in avail}; the most precise format when empty.
+int choose_format(double u_prime, uint32_t avail) {
+  int best = -1, most_precise = -1;
+  for (int p = 0; p < kPrecCount; ++p) {
+    if (!(avail >> p & 1u)) continue;
+    const double u = unit_roundoff(p);
+    if (most_precise < 0 || u < unit_roundoff(most_precise)) most_precise = p;
+    if (u <= u_prime && (best < 0 || u > unit_roundoff(best))) best = p;
+  }
+  return best >= 0 ? best : most_precise;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct hodlr_s {
+  int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
+  double eps = 0.0;
+  uint32_t avail = 0;
+  int device = 0;
+  std::vector<NodeDev> nodes;
+  std::vector<LeafDev> leaves;
+  std::vector<P1Item> p1;
+  std::vector<P2Item> p2;
+  std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
+  std::vector<int64_t> st_U, st_V, st_D; // staging offsets (elements)
+  int64_t st_count = 0;
+  hodlr_info_t info{};
+  uint8_t* d_pool = nullptr;
+  size_t pool_bytes = 0;
+  NodeDev* d_nodes = nullptr;
+  LeafDev* d_leaves = nullptr;
+  P1Item* d_p1 = nullptr;
+  P2Item* d_p2 = nullptr;
+  void* d_Y = nullptr;
+  void* d_partials = nullptr;
+  unsigned* d_counters = nullptr;
+  size_t scratch_bytes = 0;
+  HandleDev hd{};
+
+  ~hodlr_s() {
+    cudaFree(d_pool);
+    cudaFree(d_nodes);
+    cudaFree(d_leaves);
+    cudaFree(d_p1);
+    cudaFree(d_p2);
+    cudaFree(d_Y);
+    cudaFree(d_partials);
+    cudaFree(d_counters);
+  }
+};
+
+namespace {
+
+struct DevBuf {  // RAII for import-time temporaries
+  void* p = nullptr;
+  ~DevBuf() { cudaFree(p); }
+};
+
+template <typename T>
+hodlr_status upload(const std::vector<T>& v, T** dst) {
+  if (v.empty()) { *dst = nullptr; return HODLR_OK; }
+  CK(cudaMalloc((void**)dst, v.size() * sizeof(T)));
+  CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HODLR_OK;
+}
+
+// Cluster tree of Def. 2.1 with the ceil-half split of Sect. 4.
+void build_tree(int n, int depth, std::vector<std::vector<std::pair<int, int>>>& lv) {
+  lv.assign(depth + 1, {});
+  lv[0].push_back({0, n});
+  for (int k = 0; k < depth; ++k) {
+    for (auto& nd : lv[k]) {
+      const int left = (nd.second + 1) / 2;
+      lv[k + 1].push_back({nd.first, left});
+      lv[k + 1].push_back({nd.first + left, nd.second - left});
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hodlr_status_string(hodlr_status s) {
+  switch (s) {
+    case HODLR_OK: return "ok";
+    case HODLR_EINVAL: return "invalid argument";
+    case HODLR_ENOMEM: return "out of memory";
+    case HODLR_ECUDA: return "CUDA error";
+    case HODLR_ETIMEOUT: return "device wait timed out";
+    case HODLR_ENOTFACTORED: return "matrix not factored";
+    case HODLR_ESINGULAR: return "singular pivot";
+    case HODLR_EACCURACY: return "accuracy target not met";
+  }
+  return "unknown status";
+}
+
+const char* hodlr_last_error(void) { return g_last_error.c_str(); }
+
+void hodlr_destroy(hodlr_t h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  cudaSetDevice(cur);
+}
+
+hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const double* const* U,
+                          const double* const* V, const double* const* D, const hodlr_opts* opts,
+                          void* stream, hodlr_t* out) {
+  g_last_error.clear();
+  if (!out || !opts) return fail(HODLR_EINVAL, "null out/opts");
+  if (n < 1) return fail(HODLR_EINVAL, "n must be >= 1");
+  if (depth < 0 || depth > HODLR_MAX_DEPTH) return fail(HODLR_EINVAL, "depth out of range");
+  if ((int64_t(1) << depth) > n) return fail(HODLR_EINVAL, "2^depth > n (empty leaves)");
+  if (!(opts->eps >= 0.0 && opts->eps < 1.0)) return fail(HODLR_EINVAL, "eps must be in [0, 1)");
+  if (opts->work != HODLR_FP64 && opts->work != HODLR_FP32)
+    return fail(HODLR_EINVAL, "working precision must be FP64 or FP32");
+  if (opts->tier_mask >> kPrecCount) return fail(HODLR_EINVAL, "tier_mask has unknown bits");
+  if (opts->max_nrhs < 0 || opts->max_nrhs > 4096) return fail(HODLR_EINVAL, "max_nrhs out of range");
+  if (depth > 0 && (!ranks || !U || !V)) return fail(HODLR_EINVAL, "null ranks/U/V");
+  if (!D) return fail(HODLR_EINVAL, "null D");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  auto h = new hodlr_s();
+  std::unique_ptr<hodlr_s> guard(h);
+  h->n = n;
+  h->depth = depth;
+  h->work = opts->work;
+  h->per_block = opts->per_block ? 1 : 0;
+  h->eps = opts->eps;
+  h->avail = opts->tier_mask | (1u << opts->work);
+  h->max_nrhs = opts->max_nrhs ? opts->max_nrhs : 64;
+  CK(cudaGetDevice(&h->device));
+
+  std::vector<std::vector<std::pair<int, int>>> lv;
+  build_tree(n, depth, lv);
+  const int nleaves = 1 << depth;
+  const int nnodes = (1 << (depth + 1)) - 2;
+
+  // ---- leaves: padded row space ----
+  h->leaves.resize(nleaves);
+  int prow = 0, leaf_pm_max = 0;
+  for (int l = 0; l < nleaves; ++l) {
+    LeafDev& lf = h->leaves[l];
+    lf.row0 = lv[depth][l].first;
+    lf.m = lv[depth][l].second;
+    if (lf.m > kMaxLeaf) return fail(HODLR_EINVAL, "leaf larger than 1024 rows; increase depth");
+    if (!D[l]) return fail(HODLR_EINVAL, "null leaf block");
+    lf.pm = (int)align_up(lf.m, kRowPad);
+    lf.prow0 = prow;
+    lf.node = depth > 0 ? node_index(depth, l) : -1;
+    prow += lf.pm;
+    leaf_pm_max = std::max(leaf_pm_max, lf.pm);
+  }
+
+  // ---- nodes ----
+  h->nodes.resize(nnodes);
+  for (int k = 1; k <= depth; ++k) {
+    const int span = 1 << (depth - k);  // leaves per node
+    for (int i = 0; i < (1 << k); ++i) {
+      NodeDev& nd = h->nodes[node_index(k, i)];
+      memset(&nd, 0, sizeof(nd));
+      nd.level = k;
+      nd.idx = i;
+      nd.row0 = lv[k][i].first;
+      nd.m = lv[k][i].second;
+      nd.prow0 = h->leaves[i * span].prow0;
+      const LeafDev& last = h->leaves[i * span + span - 1];
+      nd.pm = last.prow0 + last.pm - nd.prow0;
+      const int rU = ranks[node_index(k, i)];
+      const int rV = ranks[node_index(k, i ^ 1)];
+      const int msib = lv[k][i ^ 1].second;
+      if (rU < 0 || rU > std::min(nd.m, msib)) return fail(HODLR_EINVAL, "rank out of range");
+      nd.rU = rU;
+      nd.rV = rV;
+      if (rU > 0 && !U[node_index(k, i)]) return fail(HODLR_EINVAL, "null U generator");
+      if (rV > 0 && !V[node_index(k, i)]) return fail(HODLR_EINVAL, "null V generator");
+    }
+  }
+
+  // ---- fp64 staging: caller's row-major matrices, back to back ----
+  h->st_U.assign(nnodes, 0);
+  h->st_V.assign(nnodes, 0);
+  h->st_D.assign(nleaves, 0);
+  int64_t off = 0;
+  for (int q = 0; q < nnodes; ++q) {
+    h->st_U[q] = off; off += (int64_t)h->nodes[q].m * h->nodes[q].rU;
+    h->st_V[q] = off; off += (int64_t)h->nodes[q].m * h->nodes[q].rV;
+  }
+  for (int l = 0; l < nleaves; ++l) { h->st_D[l] = off; off += (int64_t)h->leaves[l].m * h->leaves[l].m; }
+  h->st_count = off;
+  std::vector<double> host_stage;
+  try { host_stage.resize((size_t)off); } catch (...) { return fail(HODLR_ENOMEM, "host staging"); }
+  for (int q = 0; q < nnodes; ++q) {
+    const NodeDev& nd = h->nodes[q];
+    if (nd.rU) memcpy(&host_stage[h->st_U[q]], U[q], sizeof(double) * nd.m * nd.rU);
+    if (nd.rV) memcpy(&host_stage[h->st_V[q]], V[q], sizeof(double) * nd.m * nd.rV);
+  }
+  for (int l = 0; l < nleaves; ++l)
+    memcpy(&host_stage[h->st_D[l]], D[l], sizeof(double) * h->leaves[l].m * h->leaves[l].m);
+  DevBuf d_stage;
+  if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(off, 1)) != cudaSuccess)
+    return fail(HODLR_ENOMEM, "device staging");
+  CK(cudaMemcpyAsync(d_stage.p, host_stage.data(), sizeof(double) * off, cudaMemcpyHostToDevice, s));
+
+  // ---- norms on the device (Algorithm 3.2: nrm, nrmAll) ----
+  // tasks: [0, nnodes) V_q sum of squares + amax; [nnodes, 2 nnodes) U_q amax; then leaves.
+  std::vector<NormTask> ntasks;
+  for (int q = 0; q < nnodes; ++q) ntasks.push_back({h->st_V[q], (int64_t)h->nodes[q].m * h->nodes[q].rV});
+  for (int q = 0; q < nnodes; ++q) ntasks.push_back({h->st_U[q], (int64_t)h->nodes[q].m * h->nodes[q].rU});
+  for (int l = 0; l < nleaves; ++l) ntasks.push_back({h->st_D[l], (int64_t)h->leaves[l].m * h->leaves[l].m});
+  DevBuf d_ntasks, d_sumsq, d_amax;
+  const size_t nt = ntasks.size();
+  CK(cudaMalloc(&d_ntasks.p, nt * sizeof(NormTask)));
+  CK(cudaMalloc(&d_sumsq.p, nt * sizeof(double)));
+  CK(cudaMalloc(&d_amax.p, nt * sizeof(double)));
+  CK(cudaMemcpyAsync(d_ntasks.p, ntasks.data(), nt * sizeof(NormTask), cudaMemcpyHostToDevice, s));
+  CK(launch_norms((const double*)d_stage.p, (const NormTask*)d_ntasks.p, (int)nt,
+                  (double*)d_sumsq.p, (double*)d_amax.p, s));
+  std::vector<double> sumsq(nt), amax(nt);
+  CK(cudaMemcpyAsync(sumsq.data(), d_sumsq.p, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(amax.data(), d_amax.p, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+
+  // ---- precision rule (Algorithm 3.2) ----
+  // block (k, i) = H(I_i, I_{i^1}) ~ U_i V_{i^1}^T: ||.||_F^2 = ||V_{i^1}||_F^2.
+  double total = 0.0;
+  for (int k = 1; k <= depth; ++k)
+    for (int i = 0; i < (1 << k); ++i) total += sumsq[node_index(k, i ^ 1)];
+  for (int l = 0; l < nleaves; ++l) total += sumsq[2 * nnodes + l];
+  hodlr_info_t& inf = h->info;
+  memset(&inf, 0, sizeof(inf));
+  inf.n = n;
+  inf.depth = depth;
+  inf.work = h->work;
+  inf.per_block = h->per_block;
+  inf.n_blocks = nnodes;
+  inf.norm2_all = total;
+  std::vector<int> block_tier(nnodes, h->work);
+  for (int k = 1; k <= depth; ++k) {
+    const double lvl_scale = std::pow(2.0, k / 2.0);
+    double level_max = 0.0;
+    for (int i = 0; i < (1 << k); ++i) level_max = std::max(level_max, sumsq[node_index(k, i ^ 1)]);
+    const double xi_k = total > 0.0 ? std::sqrt(level_max / total) : 0.0;
+    const double up_k = xi_k > 0.0 ? opts->eps / (lvl_scale * xi_k) : INFINITY;
+    inf.xi[k] = xi_k;
+    inf.u_prime[k] = up_k;
+    if (!h->per_block) {
+      const int t = choose_format(up_k, h->avail);
+      inf.level_tier[k] = t;
+      for (int i = 0; i < (1 << k); ++i) block_tier[node_index(k, i)] = t;
+    } else {
+      int most = -1;
+      for (int i = 0; i < (1 << k); ++i) {
+        const double bn = sumsq[node_index(k, i ^ 1)];
+        const double xi = total > 0.0 ? std::sqrt(bn / total) : 0.0;
+        const double up = xi > 0.0 ? opts->eps / (lvl_scale * xi) : INFINITY;
+        const int t = choose_format(up, h->avail);
+        block_tier[node_index(k, i)] = t;
+        if (most < 0 || unit_roundoff(t) < unit_roundoff(most)) most = t;
+      }
+      inf.level_tier[k] = most;
+    }
+  }
+
+  // ---- pool layout ----
+  size_t pool = 0;
+  const int ebw = prec_bytes(h->work);
+  for (int k = 1; k <= depth; ++k) {
+    for (int i = 0; i < (1 << k); ++i) {
+      const int q = node_index(k, i);
+      NodeDev& nd = h->nodes[q];
+      nd.tierU = block_tier[q];
+      nd.tierV = block_tier[node_index(k, i ^ 1)];
+      const double sU = pow2_scale(amax[nnodes + q], nd.tierU);
+      const double sV = pow2_scale(amax[q], nd.tierV);
+      nd.invsU = 1.0 / sU;
+      nd.invsV = 1.0 / sV;
+      pool = align_up(pool, 256);
+      nd.offU = (int64_t)pool;
+      pool += (size_t)nd.rU * nd.pm * prec_bytes(nd.tierU);
+      pool = align_up(pool, 256);
+      nd.offV = (int64_t)pool;
+      pool += (size_t)nd.rV * nd.pm * prec_bytes(nd.tierV);
+      inf.max_rank = std::max(inf.max_rank, nd.rU);
+      const int64_t fb = (int64_t)nd.m * (nd.rU * prec_bytes(nd.tierU) + nd.rV * prec_bytes(nd.tierV));
+      inf.factor_bytes += fb;
+      inf.bytes_per_tier[nd.tierU] += (int64_t)nd.m * nd.rU * prec_bytes(nd.tierU);
+      inf.bytes_per_tier[nd.tierV] += (int64_t)nd.m * nd.rV * prec_bytes(nd.tierV);
+      if (sU != 1.0 && nd.rU) inf.scale_bytes += 8;
+      if (sV != 1.0 && nd.rV) inf.scale_bytes += 8;
+      // pack tasks: one per generator column and leaf segment (padded row space)
+      const int span = 1 << (depth - k);
+      for (int l = i * span; l < (i + 1) * span; ++l) {
+        const LeafDev& lf = h->leaves[l];
+        const int rel = lf.row0 - nd.row0, prel = lf.prow0 - nd.prow0;
+        for (int c = 0; c < nd.rU; ++c) {
+          const int ebu = prec_bytes(nd.tierU);
+          h->tasks.push_back({h->st_U[q] + (int64_t)rel * nd.rU + c, nd.rU, lf.m, lf.pm,
+                              nd.offU + ((int64_t)c * nd.pm + prel) * ebu, nd.tierU, 0, sU});
+        }
+        for (int c = 0; c < nd.rV; ++c) {
+          const int ebv = prec_bytes(nd.tierV);
+          h->tasks.push_back({h->st_V[q] + (int64_t)rel * nd.rV + c, nd.rV, lf.m, lf.pm,
+                              nd.offV + ((int64_t)c * nd.pm + prel) * ebv, nd.tierV, 0, sV});
+        }
+      }
+    }
+  }
+  for (int l = 0; l < nleaves; ++l) {
+    LeafDev& lf = h->leaves[l];
+    pool = align_up(pool, 256);
+    lf.offD = (int64_t)pool;
+    pool += (size_t)lf.m * lf.pm * ebw;
+    inf.leaf_bytes += (int64_t)lf.m * lf.m * ebw;
+    for (int j = 0; j < lf.m; ++j)
+      h->tasks.push_back({h->st_D[l] + j, lf.m, lf.m, lf.pm, lf.offD + (int64_t)j * lf.pm * ebw,
+                          h->work, 0, 1.0});
+  }
+  pool = align_up(std::max<size_t>(pool, 256), 256);
+  h->pool_bytes = pool;
+  if (cudaMalloc((void**)&h->d_pool, pool) != cudaSuccess) return fail(HODLR_ENOMEM, "factor pool");
+  CK(cudaMemsetAsync(h->d_pool, 0, pool, s));
+  {
+    DevBuf d_tasks;
+    CK(cudaMalloc(&d_tasks.p, std::max<size_t>(h->tasks.size(), 1) * sizeof(PackTask)));
+    CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask),
+                       cudaMemcpyHostToDevice, s));
+    CK(launch_pack((const double*)d_stage.p, (const PackTask*)d_tasks.p, (int)h->tasks.size(),
+                   h->d_pool, s));
+    CK(cudaStreamSynchronize(s));
+  }
+
+  // ---- work lists ----
+  int yoff = 0, poff = 0, sum_r_max = 0;
+  const int p1_leaves = std::max(1, 1024 / leaf_pm_max);  // leaves per phase-1 item
+  for (int k = 1; k <= depth; ++k) {
+    const int span = 1 << (depth - k);
+    for (int i = 0; i < (1 << k); ++i) {
+      const int q = node_index(k, i);
+      NodeDev& nd = h->nodes[q];
+      nd.yoff = yoff;
+      yoff += nd.rV;
+      if (nd.rV == 0) continue;
+      const int nitems = (span + p1_leaves - 1) / p1_leaves;
+      for (int t = 0; t < nitems; ++t) {
+        P1Item it;
+        it.node = q;
+        it.leaf0 = i * span + t * p1_leaves;
+        it.nleaf = std::min(p1_leaves, span - t * p1_leaves);
+        it.item_in_node = t;
+        it.nitems = nitems;
+        it.poff = poff;
+        poff += nd.rV;
+        h->p1.push_back(it);
+      }
+    }
+  }
+  for (int l = 0; l < nleaves; ++l) {
+    int sr = 0;
+    for (int k = 1; k <= depth; ++k) sr += h->nodes[node_index(k, l >> (depth - k))].rU;
+    sum_r_max = std::max(sum_r_max, sr);
+    for (int t0 = 0; t0 < h->leaves[l].m; t0 += kTileRows) h->p2.push_back({l, t0});
+  }
+
+  // ---- descriptors and scratch on the device ----
+  hodlr_status st;
+  if ((st = upload(h->nodes, &h->d_nodes)) != HODLR_OK) return st;
+  if ((st = upload(h->leaves, &h->d_leaves)) != HODLR_OK) return st;
+  if ((st = upload(h->p1, &h->d_p1)) != HODLR_OK) return st;
+  if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
+  const size_t yb = (size_t)std::max(yoff, 1) * h->max_nrhs * ebw;
+  const size_t pb = (size_t)std::max(poff, 1) * h->max_nrhs * ebw;
+  if (cudaMalloc(&h->d_Y, yb) != cudaSuccess) return fail(HODLR_ENOMEM, "Y scratch");
+  if (cudaMalloc(&h->d_partials, pb) != cudaSuccess) return fail(HODLR_ENOMEM, "partials scratch");
+  if (cudaMalloc((void**)&h->d_counters, sizeof(unsigned) * std::max(nnodes, 1)) != cudaSuccess)
+    return fail(HODLR_ENOMEM, "counters");
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned) * std::max(nnodes, 1), s));
+  CK(cudaStreamSynchronize(s));
+  h->scratch_bytes = yb + pb + sizeof(unsigned) * std::max(nnodes, 1);
+
+  HandleDev& hd = h->hd;
+  hd.nodes = h->d_nodes;
+  hd.leaves = h->d_leaves;
+  hd.p1 = h->d_p1;
+  hd.p2 = h->d_p2;
+  hd.pool = h->d_pool;
+  hd.n = n;
+  hd.depth = depth;
+  hd.n_nodes = nnodes;
+  hd.n_leaves = nleaves;
+  hd.n_p1 = (int)h->p1.size();
+  hd.n_p2 = (int)h->p2.size();
+  hd.y_rows = yoff;
+  hd.p_rows = poff;
+  hd.sum_r_max = sum_r_max;
+  hd.leaf_pm_max = leaf_pm_max;
+  inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
+                               h->leaves.size() * sizeof(LeafDev) + h->p1.size() * sizeof(P1Item) +
+                               h->p2.size() * sizeof(P2Item));
+  *out = guard.release();
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_export(hodlr_t h, double* const* U, double* const* V, double* const* D,
+                          void* stream) {
+  g_last_error.clear();
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf d_stage, d_tasks;
+  if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(h->st_count, 1)) != cudaSuccess)
+    return fail(HODLR_ENOMEM, "export staging");
+  CK(cudaMalloc(&d_tasks.p, std::max<size_t>(h->tasks.size(), 1) * sizeof(PackTask)));
+  CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask),
+                     cudaMemcpyHostToDevice, s));
+  CK(launch_unpack(h->d_pool, (const PackTask*)d_tasks.p, (int)h->tasks.size(),
+                   (double*)d_stage.p, s));
+  std::vector<double> host((size_t)h->st_count);
+  CK(cudaMemcpyAsync(host.data(), d_stage.p, sizeof(double) * h->st_count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int nnodes = (int)h->nodes.size();
+  for (int q = 0; q < nnodes; ++q) {
+    const NodeDev& nd = h->nodes[q];
+    if (U && U[q] && nd.rU) memcpy(U[q], &host[h->st_U[q]], sizeof(double) * nd.m * nd.rU);
+    if (V && V[q] && nd.rV) memcpy(V[q], &host[h->st_V[q]], sizeof(double) * nd.m * nd.rV);
+  }
+  for (size_t l = 0; l < h->leaves.size(); ++l)
+    if (D && D[l])
+      memcpy(D[l], &host[h->st_D[l]], sizeof(double) * h->leaves[l].m * h->leaves[l].m);
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, void* B,
+                          int64_t ldb, int32_t xb_prec, void* stream) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  if (nrhs < 0) return fail(HODLR_EINVAL, "nrhs < 0");
+  if (nrhs == 0) return HODLR_OK;
+  if (!X || !B) return fail(HODLR_EINVAL, "null X/B");
+  if (ldx < nrhs || ldb < nrhs) return fail(HODLR_EINVAL, "leading dimension < nrhs");
+  if (xb_prec != h->work) return fail(HODLR_EINVAL, "X/B type must equal the working precision");
+  const size_t es = prec_bytes(h->work);
+  const char* xb = (const char*)X;
+  char* bb = (char*)B;
+  const size_t span_x = ((size_t)(h->n - 1) * ldx + nrhs) * es, span_b = ((size_t)(h->n - 1) * ldb + nrhs) * es;
+  if (!(xb + span_x <= bb || bb + span_b <= xb)) return fail(HODLR_EINVAL, "X and B overlap");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int c0 = 0; c0 < nrhs; c0 += h->max_nrhs) {
+    const int nb = std::min(h->max_nrhs, nrhs - c0);
+    cudaError_t e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y,
+                                  h->d_partials, h->d_counters, s);
+    if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
+  }
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out) {
+  if (!h || !out) return fail(HODLR_EINVAL, "null handle/out");
+  *out = h->info;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  for (size_t q = 0; q < h->nodes.size(); ++q) {
+    if (tiers) tiers[q] = h->nodes[q].tierU;
+    if (ranks) ranks[q] = h->nodes[q].rU;
+  }
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_dense_kernel_matvec(int32_t n, int32_t dim, const double* points, int32_t kind,
+                                       double c, double len2, double diag, int32_t nrows,
+                                       const int32_t* rows, int32_t nrhs, const double* X,
+                                       int64_t ldx, double* B, int64_t ldb, void* stream) {
+  if (n < 1 || dim < 1 || dim > 3 || !points) return fail(HODLR_EINVAL, "bad n/dim/points");
+  if (kind < 0 || kind > 3 || (kind == 3 && dim != 1)) return fail(HODLR_EINVAL, "bad kernel kind");
+  if (kind == 1 && !(len2 > 0.0)) return fail(HODLR_EINVAL, "len2 must be > 0");
+  if (nrows < 0 || nrhs < 0 || (!rows && nrows != n)) return fail(HODLR_EINVAL, "bad rows");
+  if (nrows == 0 || nrhs == 0) return HODLR_OK;
+  if (!X || !B || ldx < nrhs || ldb < nrhs) return fail(HODLR_EINVAL, "bad X/B");
+  cudaError_t e = launch_dense_kernel_matvec(n, dim, points, kind, c, len2, diag, nrows, rows,
+                                             nrhs, X, ldx, B, ldb, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dense kernel matvec");
+  return HODLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+"""Python handle around the C ABI (argument marshalling only).
+
+Every step of the product runs in libhodlr's kernels; this module converts
+Python/torch arguments to pointers and sizes, and raises on a non-OK status.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from ._lib import PREC, PREC_NAME, Info, Opts, check, load
+
+_TORCH_DTYPE = {"fp64": torch.float64, "fp32": torch.float32}
+
+
+def _stream_ptr(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr_array(mats: Sequence):
+    """Array of double* for a list of C-contiguous float64 numpy arrays (None -> NULL)."""
+    arr = (ctypes.POINTER(ctypes.c_double) * max(len(mats), 1))()
+    keep = []
+    for i, m in enumerate(mats):
+        if m is None or m.size == 0:
+            arr[i] = ctypes.POINTER(ctypes.c_double)()
+            continue
+        a = np.ascontiguousarray(m, dtype=np.float64)
+        keep.append(a)
+        arr[i] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return arr, keep
+
+
+def tree_sizes(n: int, depth: int):
+    """Node sizes of the ceil-half cluster tree (levels[k][i] = (row0, m))."""
+    levels = [[(0, n)]]
+    for _ in range(depth):
+        nxt = []
+        for (s, m) in levels[-1]:
+            left = (m + 1) // 2
+            nxt += [(s, left), (s + left, m - left)]
+        levels.append(nxt)
+    return levels
+
+
+class HodlrMatrix:
+    """A stored adaptive-precision HODLR matrix on the current CUDA device."""
+
+    def __init__(self, handle: ctypes.c_void_p, n: int, depth: int, work: str):
+        self._h = handle
+        self.n, self.depth, self.work = n, depth, work
+        self.dtype = _TORCH_DTYPE[work]
+
+    # ---- construction -------------------------------------------------
+    @classmethod
+    def from_factors(cls, n: int, depth: int, ranks: Sequence[int], U: Sequence, V: Sequence,
+                     D: Sequence, eps: float, work: str = "fp32",
+                     tiers: Sequence[str] = ("fp64", "fp32", "bf16", "fp16", "e4m3"),
+                     per_block: bool = False, max_nrhs: int = 64, stream=None) -> "HodlrMatrix":
+        """hodlr_import: per-node lists in level order (level 1, then 2, ...):
+        ``ranks[q]`` = rank of block (i, i^1); ``U[q]`` (m_i x rank) and
+        ``V[q]`` (m_i x rank of the sibling's block); ``D`` per leaf."""
+        lib = load()
+        nn = (1 << (depth + 1)) - 2
+        if len(ranks) != nn or len(U) != nn or len(V) != nn or len(D) != (1 << depth):
+            raise ValueError("per-node lists must have 2^(depth+1)-2 entries and D 2^depth")
+        r = (ctypes.c_int32 * max(nn, 1))(*[int(x) for x in ranks])
+        pu, ku = _dptr_array(U)
+        pv, kv = _dptr_array(V)
+        pd, kd = _dptr_array(D)
+        mask = 0
+        for t in tiers:
+            mask |= 1 << PREC[t]
+        opts = Opts(eps=float(eps), work=PREC[work], tier_mask=mask, per_block=int(per_block),
+                    max_nrhs=int(max_nrhs))
+        h = ctypes.c_void_p()
+        check(lib.hodlr_import(n, depth, r, pu, pv, pd, ctypes.byref(opts), _stream_ptr(stream),
+                               ctypes.byref(h)), "hodlr_import")
+        del ku, kv, kd
+        return cls(h, n, depth, work)
+
+    # ---- products -----------------------------------------------------
+    def matvec(self, X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """B = H X on the device (hodlr_matvec).  X: (n,) or (n, R) CUDA tensor of
+        the working dtype, rows contiguous (stride(1) == 1)."""
+        vec = X.dim() == 1
+        X2 = X.view(-1, 1) if vec else X
+        if X2.dtype != self.dtype or not X2.is_cuda or X2.shape[0] != self.n or X2.stride(1) != 1:
+            raise ValueError("X must be a CUDA (n, R) tensor of the working dtype with unit column stride")
+        R = X2.shape[1]
+        if out is None:
+            out = torch.empty((self.n, R), dtype=self.dtype, device=X2.device)
+        B2 = out.view(-1, 1) if out.dim() == 1 else out
+        if B2.shape != (self.n, R) or B2.dtype != self.dtype or B2.stride(1) != 1:
+            raise ValueError("out has the wrong shape/dtype/layout")
+        ldx = X2.stride(0) if R > 1 else max(X2.stride(0), 1)
+        ldb = B2.stride(0) if R > 1 else max(B2.stride(0), 1)
+        check(load().hodlr_matvec(self._h, R, ctypes.c_void_p(X2.data_ptr()), ldx,
+                                  ctypes.c_void_p(B2.data_ptr()), ldb, PREC[self.work],
+                                  _stream_ptr(stream)), "hodlr_matvec")
+        return out.view(-1) if vec and out.dim() == 2 else out
+
+    # ---- inspection ---------------------------------------------------
+    def info(self) -> dict:
+        inf = Info()
+        check(load().hodlr_info(self._h, ctypes.byref(inf)), "hodlr_info")
+        d = self.depth
+        return {
+            "n": inf.n, "depth": inf.depth, "work": PREC_NAME[inf.work], "per_block": inf.per_block,
+            "max_rank": inf.max_rank, "n_blocks": inf.n_blocks,
+            "factor_bytes": inf.factor_bytes, "leaf_bytes": inf.leaf_bytes,
+            "scale_bytes": inf.scale_bytes, "device_bytes": inf.device_bytes,
+            "bytes_per_tier": {PREC_NAME[p]: inf.bytes_per_tier[p] for p in range(6)},
+            "norm2_all": inf.norm2_all,
+            "xi": [inf.xi[k] for k in range(d + 1)],
+            "u_prime": [inf.u_prime[k] for k in range(d + 1)],
+            "level_tier": [PREC_NAME.get(inf.level_tier[k], "?") if k else None for k in range(d + 1)],
+        }
+
+    def block_tiers(self):
+        nn = (1 << (self.depth + 1)) - 2
+        t = (ctypes.c_int32 * max(nn, 1))()
+        r = (ctypes.c_int32 * max(nn, 1))()
+        check(load().hodlr_block_tiers(self._h, t, r), "hodlr_block_tiers")
+        return [PREC_NAME[t[q]] for q in range(nn)], [r[q] for q in range(nn)]
+
+    def export(self, stream=None):
+        """Stored generators decoded to fp64 (hodlr_export): (U, V, D) lists."""
+        lv = tree_sizes(self.n, self.depth)
+        _tiers, ranks = self.block_tiers()
+        U, V = [], []
+        for k in range(1, self.depth + 1):
+            for i, (_s, m) in enumerate(lv[k]):
+                q = (1 << k) - 2 + i
+                qs = (1 << k) - 2 + (i ^ 1)
+                U.append(np.zeros((m, ranks[q])))
+                V.append(np.zeros((m, ranks[qs])))
+        D = [np.zeros((m, m)) for (_s, m) in lv[self.depth]]
+        pu, _ = _dptr_array(U)
+        pv, _ = _dptr_array(V)
+        pd, _ = _dptr_array(D)
+        check(load().hodlr_export(self._h, pu, pv, pd, _stream_ptr(stream)), "hodlr_export")
+        return U, V, D
+
+    def close(self):
+        if self._h:
+            load().hodlr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dense_kernel_matvec(points: torch.Tensor, kind: int, X: torch.Tensor, c: float = 0.0,
+                        len2: float = 1.0, diag: float = 0.0, rows: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+    """On-the-fly FP64 dense kernel product (hodlr_dense_kernel_matvec).
+    points: (n, dim) fp64 CUDA; X: (n, R) fp64 CUDA; rows: int32 CUDA or None."""
+    pts = points if points.dim() == 2 else points.view(-1, 1)
+    pts = pts.contiguous()
+    X2 = X.view(-1, 1) if X.dim() == 1 else X
+    X2 = X2.contiguous()
+    n, dim = pts.shape
+    nrows = n if rows is None else rows.numel()
+    B = torch.empty((nrows, X2.shape[1]), dtype=torch.float64, device=X2.device)
+    rp = ctypes.c_void_p(rows.data_ptr()) if rows is not None else ctypes.c_void_p()
+    check(load().hodlr_dense_kernel_matvec(n, dim, ctypes.c_void_p(pts.data_ptr()), kind, c, len2,
+                                           diag, nrows, rp, X2.shape[1],
+                                           ctypes.c_void_p(X2.data_ptr()), X2.shape[1],
+                                           ctypes.c_void_p(B.data_ptr()), X2.shape[1],
+                                           _stream_ptr(stream)), "hodlr_dense_kernel_matvec")
+    return B
