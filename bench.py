@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive-precision HODLR matrix-(multi)vector product on
+GB300 (Carson, Chen, Liu, "Mixed Precision HODLR Matrices", Algorithm 3.3 on
+the format of Algorithm 3.2).
+
+Workload (synthetic stand-in for the paper's kernel matrices, Sect. 4.2):
+n = 65536 points x ~ U[0,1] sorted (seed 2), Gaussian kernel
+A_ij = exp(-(x_i - x_j)^2 / 0.01) + 1e-2 delta_ij, leaf 256, depth 8,
+eps = 1e-6, storage formats {fp64, fp32, bf16, fp16, e4m3} chosen by the
+adaptive rule, fp32 working precision, right-hand sides ~ N(0,1).
+
+One step = one product for each of R = 1, 8 and 64 right-hand sides (73
+right-hand sides in all), each on inputs already resident in HBM; the L2
+cache is flushed (a 2x L2-size write, untimed) before every product and each
+product is timed with CUDA events on its stream.  The metric is RHS*rows/s
+(sum over the step of R*n divided by the step's device time).
+
+The matrix is built on the GPU by hodlr_build (untimed setup).  Reported
+beside it: the roofline of the dominant kernel, the same product through
+host buffers (e2e), the plain FP64 GPU HODLR of the same eps (Algorithm 3.2
+with fp64 only), backward errors against the dense kernel matrix, and the CPU
+oracle timed on this host's cores on a bounded sample.
+
+--impl reference times the CPU oracle (the reference arm of this workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HODLR matvec RHS·rows/s & HBM GB/s, adaptive vs FP64 GPU at equal error"
+UNIT = "RHS*rows/s"
+WL = dict(name="gauss_65536", n=65536, leaf=256, depth=8, eps=1e-6, kind=1, len2=0.01, diag=1e-2,
+          c=0.0, seed=2, work="fp32", tiers=("fp64", "fp32", "bf16", "fp16", "e4m3"), rhs=(1, 8, 64))
+# Bounded CPU sample: the leading diagonal block H_11^(4) of the same matrix
+# (n/16 rows, the same kernel, leaf size, eps and formats; depth 4).
+SAMPLE_DIV = 16
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_sample(min_seconds: float = 10.0, steps: int | None = None):
+    """Time the CPU oracle's Algorithm 3.3 on the bounded sample: the leading
+    diagonal block of the workload (n/16 rows), built by the oracle itself."""
+    import synth
+    from oracle import compress as C
+    from oracle import matvec as M
+
+    n = WL["n"] // SAMPLE_DIV
+    depth = WL["depth"] - int(math.log2(SAMPLE_DIV))
+    pts = synth.uniform_points_1d(WL["n"], WL["seed"])[:n]
+    spec = synth.KernelSpec(WL["kind"], c=WL["c"], len2=WL["len2"], diag=WL["diag"])
+    h = C.adaptive_hodlr(pts, spec, n, depth, WL["eps"], work=WL["work"], tiers=WL["tiers"])
+    Xs = {R: synth.rhs_normal(n, R, 7 + R).astype(np.float64) for R in WL["rhs"]}
+    for R in WL["rhs"]:                       # warm-up
+        M.hodlr_matvec(h, Xs[R])
+    times = []
+    t_end = time.perf_counter() + min_seconds
+    while True:
+        t0 = time.perf_counter()
+        for R in WL["rhs"]:
+            M.hodlr_matvec(h, Xs[R])
+        times.append(time.perf_counter() - t0)
+        if steps is not None and len(times) >= steps:
+            break
+        if steps is None and time.perf_counter() >= t_end and len(times) >= 3:
+            break
+    per_step = float(np.mean(times))
+    units = sum(WL["rhs"]) * n
+    cores = _cpu_threads()
+    return {"value": units / per_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle (numpy fp64, Algorithm 3.3) on the leading diagonal block H_11^(4) of the "
+                      f"workload: n={n}, depth={depth}, same kernel/eps/formats, R in {list(WL['rhs'])}; "
+                      f"{len(times)} steps, {per_step * 1e3:.1f} ms/step",
+            "ms_per_step": per_step * 1e3}
+
+
+def _cpu_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
+    except Exception:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    t0 = time.perf_counter()
+    base = cpu_oracle_sample(min_seconds=0.0, steps=args.warmup)  # warm-up steps (includes build)
+    res = cpu_oracle_sample(min_seconds=0.0, steps=args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{WL['name']} (bounded sample: leading diagonal block n={WL['n'] // SAMPLE_DIV})",
+                   "n": WL["n"], "leaf": WL["leaf"], "depth": WL["depth"], "eps": WL["eps"],
+                   "rhs": list(WL["rhs"])},
+        "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t0,
+    }
+    del base
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import torch
+
+    import synth
+    from paper_2407_21637_gb300 import HodlrMatrix, dense_kernel_matvec
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = WL["n"]
+    pts_np = synth.uniform_points_1d(n, WL["seed"])
+    pts = torch.from_numpy(pts_np).to(dev)
+    t_build = time.perf_counter()
+    g = HodlrMatrix.build(pts, WL["kind"], WL["depth"], WL["eps"], c=WL["c"], len2=WL["len2"],
+                          diag=WL["diag"], work=WL["work"], tiers=WL["tiers"], max_nrhs=64, seed=1)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    info = g.info()
+    es = 4
+    rhs = WL["rhs"]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + rank)
+    Xs = {R: torch.randn(n, R, device=dev, dtype=torch.float32, generator=gen) for R in rhs}
+    Bs = {R: torch.empty(n, R, device=dev, dtype=torch.float32) for R in rhs}
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(hm, Xd, Bd, ev_log=None, prof=None):
+        tot = 0.0
+        for R in rhs:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hm.matvec(Xd[R], out=Bd[R])
+            e1.record(stream)
+            if ev_log is not None:
+                ev_log.append((R, e0, e1))
+            if prof is not None:
+                prof.setdefault(R, []).append(hm.profile_read())
+        return tot
+
+    # ---- warm-up, then exactly K timed steps ----
+    for _ in range(args.warmup):
+        step(g, Xs, Bs)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]) if False else dev.index)
+    clocks.start()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    log = []
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        step(g, Xs, Bs, ev_log=log)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    per_R = {R: [] for R in rhs}
+    for (R, e0, e1) in log:
+        per_R[R].append(e0.elapsed_time(e1))
+    ms_step = float(sum(np.mean(per_R[R]) for R in rhs))
+    if dist is not None:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    units_rank = sum(rhs) * n
+    value = world * units_rank / (ms_step * 1e-3)
+
+    # ---- per-kernel profile (separate untimed pass, same flush discipline) ----
+    g.profile(True)
+    prof = {}
+    for _ in range(max(3, min(args.steps, 10))):
+        step(g, Xs, Bs, prof=prof)
+    g.profile(False)
+    peak, peak_kind = _peaks()
+    alg = {}
+    k_bytes = 0.0
+    k_ms = 0.0
+    per_rhs = {}
+    for R in rhs:
+        p1 = float(np.mean([a for a, _ in prof[R]]))
+        p2 = float(np.mean([b for _, b in prof[R]]))
+        total_bytes = info["factor_bytes"] + info["leaf_bytes"] + info["scale_bytes"] + 2 * n * R * es
+        p2_bytes = info["u_bytes"] + info["leaf_bytes"] + 2 * n * R * es   # U, D, X (leaf rows), B
+        ms = float(np.mean(per_R[R]))
+        per_rhs[str(R)] = {"us": ms * 1e3, "GBps": total_bytes / (ms * 1e-3) / 1e9,
+                           "frac_hbm": total_bytes / (ms * 1e-3) / 1e9 / peak,
+                           "phase1_us": p1 * 1e3, "phase2_us": p2 * 1e3,
+                           "phase2_GBps": p2_bytes / (p2 * 1e-3) / 1e9,
+                           "alg_bytes": total_bytes}
+        k_bytes += p2_bytes
+        k_ms += p2
+    achieved = k_bytes / (k_ms * 1e-3) / 1e9
+
+    # ---- e2e: host buffers, copies inside the timed region ----
+    Xh = {R: Xs[R].cpu().pin_memory() for R in rhs}
+    Bh = {R: torch.empty(n, R, dtype=torch.float32).pin_memory() for R in rhs}
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        tot = 0.0
+        for R in rhs:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Xs[R].copy_(Xh[R], non_blocking=True)
+            g.matvec(Xs[R], out=Bs[R])
+            Bh[R].copy_(Bs[R], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        if it >= args.warmup:
+            e2e_ms.append(tot)
+    e2e_step = float(np.mean(e2e_ms))
+    if dist is not None:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    io_bytes = sum(n * R * es for R in rhs)
+
+    # ---- backward errors against the dense kernel matrix, FP64 HODLR at equal eps ----
+    extra = {}
+    if rank == 0 and not args.quick:
+        x64 = torch.randn(n, 1, device=dev, dtype=torch.float64, generator=gen)
+        ax = dense_kernel_matvec(pts, WL["kind"], x64, c=WL["c"], len2=WL["len2"], diag=WL["diag"])
+        normA = math.sqrt(info["norm2_all"])
+        bad = g.matvec(x64.float()).double()
+        be_adapt = float(torch.linalg.norm(bad - ax) / (normA * torch.linalg.norm(x64)))
+        g64 = HodlrMatrix.build(pts, WL["kind"], WL["depth"], WL["eps"], c=WL["c"], len2=WL["len2"],
+                                diag=WL["diag"], work="fp64", tiers=("fp64",), max_nrhs=64, seed=1)
+        b64 = g64.matvec(x64)
+        be_64 = float(torch.linalg.norm(b64 - ax) / (normA * torch.linalg.norm(x64)))
+        X64 = {R: Xs[R].double() for R in rhs}
+        B64 = {R: torch.empty(n, R, device=dev, dtype=torch.float64) for R in rhs}
+        step(g64, X64, B64)
+        lg = []
+        for _ in range(max(2, min(args.steps, 5))):
+            step(g64, X64, B64, ev_log=lg)
+        torch.cuda.synchronize()
+        pr = {R: [] for R in rhs}
+        for (R, e0, e1) in lg:
+            pr[R].append(e0.elapsed_time(e1))
+        ms64 = float(sum(np.mean(pr[R]) for R in rhs))
+        i64 = g64.info()
+        extra["fp64_hodlr"] = {
+            "value": units_rank / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+            "per_rhs_us": {str(R): float(np.mean(pr[R])) * 1e3 for R in rhs},
+            "backward_error": be_64, "eps": WL["eps"],
+            "stored_bytes": i64["factor_bytes"] + i64["leaf_bytes"],
+            "speedup_adaptive_over_fp64": (units_rank / (ms_step * 1e-3)) / (units_rank / (ms64 * 1e-3)),
+            "note": "same eps; backward errors ||b^-Ax||/(||A||_F||x||) against the on-the-fly FP64 dense "
+                    "kernel product, R=1"}
+        extra["backward_error_adaptive"] = be_adapt
+        g64.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+        "config": {"workload": f"{WL['name']}: Gaussian kernel exp(-r^2/0.01)+1e-2*I on 65536 sorted U[0,1] "
+                               f"points, leaf 256, depth 8, eps 1e-6, adaptive formats "
+                               f"{{fp64,fp32,bf16,fp16,e4m3}}, fp32 work; one step = R in (1, 8, 64)",
+                   "n": n, "leaf": WL["leaf"], "depth": WL["depth"], "eps": WL["eps"], "rhs": list(rhs),
+                   "l2": "flushed (2x L2 write, untimed) before every product; products timed with CUDA events",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "phase2_kernel (leaf D X + U Y)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind,
+                     "bytes_per_launch": "U bytes + leaf bytes + n*R*4 (X) + n*R*4 (B)"},
+        "per_rhs": per_rhs,
+        "storage": {"factor_bytes": info["factor_bytes"], "leaf_bytes": info["leaf_bytes"],
+                    "bytes_per_tier": info["bytes_per_tier"], "max_rank": info["max_rank"],
+                    "level_tier": info["level_tier"][1:], "u_prime": info["u_prime"][1:],
+                    "build_s": t_build},
+        "e2e": {"value": world * units_rank / (e2e_step * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                "ms_per_step": e2e_step},
+        "gpu_launches": args.steps * len(rhs) * (2 if WL["depth"] > 0 else 1),
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        "wall_timed_s": t_wall,
+    }
+    line.update(extra)
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(min_seconds=args.cpu_seconds)
+        line["cpu_baseline"].pop("ms_per_step", None)
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and error checks")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    try:
+        return run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -88,6 +88,7 @@ typedef struct {
   int32_t max_rank;                 /* largest off-diagonal rank */
   int32_t n_blocks;                 /* 2^(depth+1) - 2 off-diagonal blocks */
   int64_t factor_bytes;             /* algorithmic bytes of U and V (no padding) */
+  int64_t u_bytes, v_bytes;         /* the U and the V part of factor_bytes */
   int64_t leaf_bytes;               /* algorithmic bytes of the leaves */
   int64_t scale_bytes;              /* 8 bytes per block with a power-of-two scale */
   int64_t device_bytes;             /* bytes the handle holds on the device */
@@ -132,6 +133,46 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks,
                           const double* const* D, const hodlr_opts* opts,
                           void* stream, hodlr_t* out);
 
+/* Kernel matrix A_ij = f(x_i, x_j) + diag * delta_ij (eq. (4.1) kernels and
+ * the synthetic workloads).  f at i == j is f(0) where finite, else 0.
+ *   kind 0  f = 1/(r + c)           kind 1  f = exp(-r^2 / len2)
+ *   kind 2  f = log(r + c)          kind 3  f = 1/(x_i - x_j)  (dim 1 only)
+ * r = ||x_i - x_j||_2 over dim in {1, 2, 3} coordinates. */
+typedef struct {
+  int32_t kind, dim;
+  double c, len2, diag;
+} hodlr_kernel;
+
+/* Randomized range finder settings of hodlr_build. */
+typedef struct {
+  int32_t sketch;      /* first sketch size per block (0 -> 16) */
+  int32_t max_sketch;  /* largest sketch size, <= 64 (0 -> 64) */
+  uint64_t seed;       /* seed of the Gaussian test matrix */
+} hodlr_build_opts;
+
+/* hodlr_build -- construct the adaptive-precision HODLR matrix of a kernel
+ * matrix on the GPU (Algorithm 3.2): every off-diagonal block is compressed
+ * to relative Frobenius accuracy eps (Def. 2.3) by a randomized range finder
+ * whose matrix entries are generated in registers (never stored): sketch
+ * Y = A_b Omega, Q = orth(Y) (shifted Cholesky QR + two Cholesky QR passes),
+ * B = Q^T A_b, the sketch residual ||A_b - Q Q^T A_b||_F computed from
+ * regenerated entries, and a one-sided Jacobi SVD of B's triangular factor;
+ * the rank is the smallest r whose SVD tail plus sketch residual is within
+ * eps ||A_b||_F.  A block whose sketch residual exceeds a quarter of that
+ * budget is redone with a doubled sketch.  The block norms ||A_b||_F and
+ * ||A||_F of Algorithm 3.2 are exact (computed from the generated entries).
+ * Then the precision rule and storage of hodlr_import apply.
+ *
+ *  points  device, (n, kernel->dim) fp64 row-major, in tree order.
+ *  bopts   may be NULL (defaults).
+ *  stream  used for all work; the call synchronises it.
+ * Returns HODLR_EACCURACY (with a valid handle in *out) when some block still
+ * exceeded its budget at the largest sketch; its rank is then the sketch
+ * size.  Other errors leave *out unchanged. */
+hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel* kernel,
+                         const double* points, const hodlr_opts* opts,
+                         const hodlr_build_opts* bopts, void* stream, hodlr_t* out);
+
 /* hodlr_export -- read the stored generators back, decoded to fp64 (the
  * values Algorithm 3.3 multiplies by: stored / scale).  Same layouts as
  * hodlr_import; any of U, V, D may be NULL to skip it.  Synchronous. */
@@ -156,6 +197,18 @@ hodlr_status hodlr_export(hodlr_t h, double* const* U, double* const* V,
  * enqueue them on one stream.  Errors: HODLR_EINVAL, HODLR_ECUDA. */
 hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, int32_t xb_prec, void* stream);
+
+/* hodlr_profile -- enable (1) or disable (0) CUDA-event timing of the
+ * kernels launched by the following hodlr_matvec calls on this handle (events
+ * are recorded on the call's stream around each kernel of its last column
+ * batch; recording costs a few microseconds of host time per call). */
+hodlr_status hodlr_profile(hodlr_t h, int32_t enable);
+
+/* hodlr_profile_read -- device time in ms of each kernel of the last
+ * profiled hodlr_matvec: ms[0] = phase 1 (V^T X, all levels), ms[1] = phase 2
+ * (leaf products and U Y).  count >= 2.  Waits for that call's events.
+ * HODLR_EINVAL when profiling is off or nothing was profiled yet. */
+hodlr_status hodlr_profile_read(hodlr_t h, float* ms, int32_t count);
 
 /* hodlr_info -- sizes, bytes per tier and the precision rule's quantities. */
 hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out);

@@ -31,11 +31,22 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("depth", ctypes.c_int32), ("work", ctypes.c_int32),
                 ("per_block", ctypes.c_int32), ("max_rank", ctypes.c_int32),
                 ("n_blocks", ctypes.c_int32), ("factor_bytes", ctypes.c_int64),
+                ("u_bytes", ctypes.c_int64), ("v_bytes", ctypes.c_int64),
                 ("leaf_bytes", ctypes.c_int64), ("scale_bytes", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("bytes_per_tier", ctypes.c_int64 * 6),
                 ("norm2_all", ctypes.c_double), ("xi", ctypes.c_double * (MAX_DEPTH + 1)),
                 ("u_prime", ctypes.c_double * (MAX_DEPTH + 1)),
                 ("level_tier", ctypes.c_int32 * (MAX_DEPTH + 1))]
+
+
+class Kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("c", ctypes.c_double),
+                ("len2", ctypes.c_double), ("diag", ctypes.c_double)]
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("sketch", ctypes.c_int32), ("max_sketch", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 # name -> (restype, argtypes); every symbol the header declares
@@ -46,10 +57,15 @@ _I32P = ctypes.POINTER(ctypes.c_int32)
 SIGNATURES = {
     "hodlr_import": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _I32P, _DP, _DP, _DP,
                                     ctypes.POINTER(Opts), _P, ctypes.POINTER(_P)]),
+    "hodlr_build": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Kernel), _P,
+                                   ctypes.POINTER(Opts), ctypes.POINTER(BuildOpts), _P,
+                                   ctypes.POINTER(_P)]),
     "hodlr_export": (ctypes.c_int, [_P, _DP, _DP, _DP, _P]),
     "hodlr_matvec": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                     ctypes.c_int32, _P]),
     "hodlr_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "hodlr_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "hodlr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "hodlr_block_tiers": (ctypes.c_int, [_P, _I32P, _I32P]),
     "hodlr_dense_kernel_matvec": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "hodlr_internal.cuh"
+#include "handle.cuh"
 
 using namespace hodlr;
 
@@ -79,42 +79,6 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
-struct hodlr_s {
-  int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
-  double eps = 0.0;
-  uint32_t avail = 0;
-  int device = 0;
-  std::vector<NodeDev> nodes;
-  std::vector<LeafDev> leaves;
-  std::vector<P1Item> p1;
-  std::vector<P2Item> p2;
-  std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
-  std::vector<int64_t> st_U, st_V, st_D; // staging offsets (elements)
-  int64_t st_count = 0;
-  hodlr_info_t info{};
-  uint8_t* d_pool = nullptr;
-  size_t pool_bytes = 0;
-  NodeDev* d_nodes = nullptr;
-  LeafDev* d_leaves = nullptr;
-  P1Item* d_p1 = nullptr;
-  P2Item* d_p2 = nullptr;
-  void* d_Y = nullptr;
-  void* d_partials = nullptr;
-  unsigned* d_counters = nullptr;
-  size_t scratch_bytes = 0;
-  HandleDev hd{};
-
-  ~hodlr_s() {
-    cudaFree(d_pool);
-    cudaFree(d_nodes);
-    cudaFree(d_leaves);
-    cudaFree(d_p1);
-    cudaFree(d_p2);
-    cudaFree(d_Y);
-    cudaFree(d_partials);
-    cudaFree(d_counters);
-  }
-};
 
 namespace {
 
@@ -146,39 +110,12 @@ void build_tree(int n, int depth, std::vector<std::vector<std::pair<int, int>>>&
 
 }  // namespace
 
-extern "C" {
+namespace hodlr {
 
-const char* hodlr_status_string(hodlr_status s) {
-  switch (s) {
-    case HODLR_OK: return "ok";
-    case HODLR_EINVAL: return "invalid argument";
-    case HODLR_ENOMEM: return "out of memory";
-    case HODLR_ECUDA: return "CUDA error";
-    case HODLR_ETIMEOUT: return "device wait timed out";
-    case HODLR_ENOTFACTORED: return "matrix not factored";
-    case HODLR_ESINGULAR: return "singular pivot";
-    case HODLR_EACCURACY: return "accuracy target not met";
-  }
-  return "unknown status";
-}
+hodlr_status set_error(hodlr_status s, const std::string& msg) { return fail(s, msg); }
+hodlr_status set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 
-const char* hodlr_last_error(void) { return g_last_error.c_str(); }
-
-void hodlr_destroy(hodlr_t h) {
-  if (!h) return;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  cudaSetDevice(h->device);
-  cudaDeviceSynchronize();
-  delete h;
-  cudaSetDevice(cur);
-}
-
-hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const double* const* U,
-                          const double* const* V, const double* const* D, const hodlr_opts* opts,
-                          void* stream, hodlr_t* out) {
-  g_last_error.clear();
-  if (!out || !opts) return fail(HODLR_EINVAL, "null out/opts");
+hodlr_status plan_layout(hodlr_s* h, int n, int depth, const int32_t* ranks, const hodlr_opts* opts) {
   if (n < 1) return fail(HODLR_EINVAL, "n must be >= 1");
   if (depth < 0 || depth > HODLR_MAX_DEPTH) return fail(HODLR_EINVAL, "depth out of range");
   if ((int64_t(1) << depth) > n) return fail(HODLR_EINVAL, "2^depth > n (empty leaves)");
@@ -187,12 +124,7 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
     return fail(HODLR_EINVAL, "working precision must be FP64 or FP32");
   if (opts->tier_mask >> kPrecCount) return fail(HODLR_EINVAL, "tier_mask has unknown bits");
   if (opts->max_nrhs < 0 || opts->max_nrhs > 4096) return fail(HODLR_EINVAL, "max_nrhs out of range");
-  if (depth > 0 && (!ranks || !U || !V)) return fail(HODLR_EINVAL, "null ranks/U/V");
-  if (!D) return fail(HODLR_EINVAL, "null D");
-  cudaStream_t s = (cudaStream_t)stream;
-
-  auto h = new hodlr_s();
-  std::unique_ptr<hodlr_s> guard(h);
+  if (depth > 0 && !ranks) return fail(HODLR_EINVAL, "null ranks");
   h->n = n;
   h->depth = depth;
   h->work = opts->work;
@@ -201,29 +133,26 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   h->avail = opts->tier_mask | (1u << opts->work);
   h->max_nrhs = opts->max_nrhs ? opts->max_nrhs : 64;
   CK(cudaGetDevice(&h->device));
-
-  std::vector<std::vector<std::pair<int, int>>> lv;
-  build_tree(n, depth, lv);
+  build_tree(n, depth, h->lv);
+  const auto& lv = h->lv;
   const int nleaves = 1 << depth;
   const int nnodes = (1 << (depth + 1)) - 2;
 
-  // ---- leaves: padded row space ----
+  // leaves: padded row space
   h->leaves.resize(nleaves);
-  int prow = 0, leaf_pm_max = 0;
+  int prow = 0;
   for (int l = 0; l < nleaves; ++l) {
     LeafDev& lf = h->leaves[l];
+    memset(&lf, 0, sizeof(lf));
     lf.row0 = lv[depth][l].first;
     lf.m = lv[depth][l].second;
     if (lf.m > kMaxLeaf) return fail(HODLR_EINVAL, "leaf larger than 1024 rows; increase depth");
-    if (!D[l]) return fail(HODLR_EINVAL, "null leaf block");
     lf.pm = (int)align_up(lf.m, kRowPad);
     lf.prow0 = prow;
     lf.node = depth > 0 ? node_index(depth, l) : -1;
     prow += lf.pm;
-    leaf_pm_max = std::max(leaf_pm_max, lf.pm);
   }
-
-  // ---- nodes ----
+  // nodes
   h->nodes.resize(nnodes);
   for (int k = 1; k <= depth; ++k) {
     const int span = 1 << (depth - k);  // leaves per node
@@ -243,12 +172,9 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
       if (rU < 0 || rU > std::min(nd.m, msib)) return fail(HODLR_EINVAL, "rank out of range");
       nd.rU = rU;
       nd.rV = rV;
-      if (rU > 0 && !U[node_index(k, i)]) return fail(HODLR_EINVAL, "null U generator");
-      if (rV > 0 && !V[node_index(k, i)]) return fail(HODLR_EINVAL, "null V generator");
     }
   }
-
-  // ---- fp64 staging: caller's row-major matrices, back to back ----
+  // fp64 staging: the row-major generators back to back, then the leaves
   h->st_U.assign(nnodes, 0);
   h->st_V.assign(nnodes, 0);
   h->st_D.assign(nleaves, 0);
@@ -259,19 +185,15 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   }
   for (int l = 0; l < nleaves; ++l) { h->st_D[l] = off; off += (int64_t)h->leaves[l].m * h->leaves[l].m; }
   h->st_count = off;
-  std::vector<double> host_stage;
-  try { host_stage.resize((size_t)off); } catch (...) { return fail(HODLR_ENOMEM, "host staging"); }
-  for (int q = 0; q < nnodes; ++q) {
-    const NodeDev& nd = h->nodes[q];
-    if (nd.rU) memcpy(&host_stage[h->st_U[q]], U[q], sizeof(double) * nd.m * nd.rU);
-    if (nd.rV) memcpy(&host_stage[h->st_V[q]], V[q], sizeof(double) * nd.m * nd.rV);
-  }
-  for (int l = 0; l < nleaves; ++l)
-    memcpy(&host_stage[h->st_D[l]], D[l], sizeof(double) * h->leaves[l].m * h->leaves[l].m);
-  DevBuf d_stage;
-  if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(off, 1)) != cudaSuccess)
-    return fail(HODLR_ENOMEM, "device staging");
-  CK(cudaMemcpyAsync(d_stage.p, host_stage.data(), sizeof(double) * off, cudaMemcpyHostToDevice, s));
+  return HODLR_OK;
+}
+
+hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double* block_norm2,
+                                 const double* leaf_norm2, const hodlr_opts* opts, cudaStream_t s) {
+  const int depth = h->depth, n = h->n;
+  const int nleaves = (int)h->leaves.size(), nnodes = (int)h->nodes.size();
+  int leaf_pm_max = 0;
+  for (const LeafDev& lf : h->leaves) leaf_pm_max = std::max(leaf_pm_max, lf.pm);
 
   // ---- norms on the device (Algorithm 3.2: nrm, nrmAll) ----
   // tasks: [0, nnodes) V_q sum of squares + amax; [nnodes, 2 nnodes) U_q amax; then leaves.
@@ -285,19 +207,25 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   CK(cudaMalloc(&d_sumsq.p, nt * sizeof(double)));
   CK(cudaMalloc(&d_amax.p, nt * sizeof(double)));
   CK(cudaMemcpyAsync(d_ntasks.p, ntasks.data(), nt * sizeof(NormTask), cudaMemcpyHostToDevice, s));
-  CK(launch_norms((const double*)d_stage.p, (const NormTask*)d_ntasks.p, (int)nt,
-                  (double*)d_sumsq.p, (double*)d_amax.p, s));
+  CK(launch_norms(d_stage, (const NormTask*)d_ntasks.p, (int)nt, (double*)d_sumsq.p,
+                  (double*)d_amax.p, s));
   std::vector<double> sumsq(nt), amax(nt);
   CK(cudaMemcpyAsync(sumsq.data(), d_sumsq.p, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(amax.data(), d_amax.p, nt * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
 
   // ---- precision rule (Algorithm 3.2) ----
-  // block (k, i) = H(I_i, I_{i^1}) ~ U_i V_{i^1}^T: ||.||_F^2 = ||V_{i^1}||_F^2.
+  // block (k, i) = H(I_i, I_{i^1}) ~ U_i V_{i^1}^T: ||.||_F^2 = ||V_{i^1}||_F^2
+  // from the factors, or the original block norm when given.
+  std::vector<double> bn(nnodes, 0.0);
   double total = 0.0;
   for (int k = 1; k <= depth; ++k)
-    for (int i = 0; i < (1 << k); ++i) total += sumsq[node_index(k, i ^ 1)];
-  for (int l = 0; l < nleaves; ++l) total += sumsq[2 * nnodes + l];
+    for (int i = 0; i < (1 << k); ++i) {
+      const int q = node_index(k, i);
+      bn[q] = block_norm2 ? block_norm2[q] : sumsq[node_index(k, i ^ 1)];
+      total += bn[q];
+    }
+  for (int l = 0; l < nleaves; ++l) total += leaf_norm2 ? leaf_norm2[l] : sumsq[2 * nnodes + l];
   hodlr_info_t& inf = h->info;
   memset(&inf, 0, sizeof(inf));
   inf.n = n;
@@ -310,7 +238,7 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   for (int k = 1; k <= depth; ++k) {
     const double lvl_scale = std::pow(2.0, k / 2.0);
     double level_max = 0.0;
-    for (int i = 0; i < (1 << k); ++i) level_max = std::max(level_max, sumsq[node_index(k, i ^ 1)]);
+    for (int i = 0; i < (1 << k); ++i) level_max = std::max(level_max, bn[node_index(k, i)]);
     const double xi_k = total > 0.0 ? std::sqrt(level_max / total) : 0.0;
     const double up_k = xi_k > 0.0 ? opts->eps / (lvl_scale * xi_k) : INFINITY;
     inf.xi[k] = xi_k;
@@ -322,8 +250,7 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
     } else {
       int most = -1;
       for (int i = 0; i < (1 << k); ++i) {
-        const double bn = sumsq[node_index(k, i ^ 1)];
-        const double xi = total > 0.0 ? std::sqrt(bn / total) : 0.0;
+        const double xi = total > 0.0 ? std::sqrt(bn[node_index(k, i)] / total) : 0.0;
         const double up = xi > 0.0 ? opts->eps / (lvl_scale * xi) : INFINITY;
         const int t = choose_format(up, h->avail);
         block_tier[node_index(k, i)] = t;
@@ -336,6 +263,7 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   // ---- pool layout ----
   size_t pool = 0;
   const int ebw = prec_bytes(h->work);
+  h->tasks.clear();
   for (int k = 1; k <= depth; ++k) {
     for (int i = 0; i < (1 << k); ++i) {
       const int q = node_index(k, i);
@@ -353,8 +281,9 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
       nd.offV = (int64_t)pool;
       pool += (size_t)nd.rV * nd.pm * prec_bytes(nd.tierV);
       inf.max_rank = std::max(inf.max_rank, nd.rU);
-      const int64_t fb = (int64_t)nd.m * (nd.rU * prec_bytes(nd.tierU) + nd.rV * prec_bytes(nd.tierV));
-      inf.factor_bytes += fb;
+      inf.factor_bytes += (int64_t)nd.m * (nd.rU * prec_bytes(nd.tierU) + nd.rV * prec_bytes(nd.tierV));
+      inf.u_bytes += (int64_t)nd.m * nd.rU * prec_bytes(nd.tierU);
+      inf.v_bytes += (int64_t)nd.m * nd.rV * prec_bytes(nd.tierV);
       inf.bytes_per_tier[nd.tierU] += (int64_t)nd.m * nd.rU * prec_bytes(nd.tierU);
       inf.bytes_per_tier[nd.tierV] += (int64_t)nd.m * nd.rV * prec_bytes(nd.tierV);
       if (sU != 1.0 && nd.rU) inf.scale_bytes += 8;
@@ -396,14 +325,15 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
     CK(cudaMalloc(&d_tasks.p, std::max<size_t>(h->tasks.size(), 1) * sizeof(PackTask)));
     CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask),
                        cudaMemcpyHostToDevice, s));
-    CK(launch_pack((const double*)d_stage.p, (const PackTask*)d_tasks.p, (int)h->tasks.size(),
-                   h->d_pool, s));
+    CK(launch_pack(d_stage, (const PackTask*)d_tasks.p, (int)h->tasks.size(), h->d_pool, s));
     CK(cudaStreamSynchronize(s));
   }
 
   // ---- work lists ----
   int yoff = 0, poff = 0, sum_r_max = 0;
   const int p1_leaves = std::max(1, 1024 / leaf_pm_max);  // leaves per phase-1 item
+  h->p1.clear();
+  h->p2.clear();
   for (int k = 1; k <= depth; ++k) {
     const int span = 1 << (depth - k);
     for (int i = 0; i < (1 << k); ++i) {
@@ -468,6 +398,75 @@ hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const 
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
                                h->leaves.size() * sizeof(LeafDev) + h->p1.size() * sizeof(P1Item) +
                                h->p2.size() * sizeof(P2Item));
+  return HODLR_OK;
+}
+
+}  // namespace hodlr
+
+extern "C" {
+
+const char* hodlr_status_string(hodlr_status s) {
+  switch (s) {
+    case HODLR_OK: return "ok";
+    case HODLR_EINVAL: return "invalid argument";
+    case HODLR_ENOMEM: return "out of memory";
+    case HODLR_ECUDA: return "CUDA error";
+    case HODLR_ETIMEOUT: return "device wait timed out";
+    case HODLR_ENOTFACTORED: return "matrix not factored";
+    case HODLR_ESINGULAR: return "singular pivot";
+    case HODLR_EACCURACY: return "accuracy target not met";
+  }
+  return "unknown status";
+}
+
+const char* hodlr_last_error(void) { return g_last_error.c_str(); }
+
+void hodlr_destroy(hodlr_t h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  cudaSetDevice(cur);
+}
+
+hodlr_status hodlr_import(int32_t n, int32_t depth, const int32_t* ranks, const double* const* U,
+                          const double* const* V, const double* const* D, const hodlr_opts* opts,
+                          void* stream, hodlr_t* out) {
+  g_last_error.clear();
+  if (!out || !opts) return fail(HODLR_EINVAL, "null out/opts");
+  if (depth > 0 && (!ranks || !U || !V)) return fail(HODLR_EINVAL, "null ranks/U/V");
+  if (!D) return fail(HODLR_EINVAL, "null D");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto h = new hodlr_s();
+  std::unique_ptr<hodlr_s> guard(h);
+  hodlr_status st = plan_layout(h, n, depth, ranks, opts);
+  if (st != HODLR_OK) return st;
+  const int nnodes = (int)h->nodes.size(), nleaves = (int)h->leaves.size();
+  for (int q = 0; q < nnodes; ++q) {
+    if (h->nodes[q].rU > 0 && !U[q]) return fail(HODLR_EINVAL, "null U generator");
+    if (h->nodes[q].rV > 0 && !V[q]) return fail(HODLR_EINVAL, "null V generator");
+  }
+  for (int l = 0; l < nleaves; ++l)
+    if (!D[l]) return fail(HODLR_EINVAL, "null leaf block");
+
+  std::vector<double> host_stage;
+  try { host_stage.resize((size_t)h->st_count); } catch (...) { return fail(HODLR_ENOMEM, "host staging"); }
+  for (int q = 0; q < nnodes; ++q) {
+    const NodeDev& nd = h->nodes[q];
+    if (nd.rU) memcpy(&host_stage[h->st_U[q]], U[q], sizeof(double) * nd.m * nd.rU);
+    if (nd.rV) memcpy(&host_stage[h->st_V[q]], V[q], sizeof(double) * nd.m * nd.rV);
+  }
+  for (int l = 0; l < nleaves; ++l)
+    memcpy(&host_stage[h->st_D[l]], D[l], sizeof(double) * h->leaves[l].m * h->leaves[l].m);
+  DevBuf d_stage;
+  if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(h->st_count, 1)) != cudaSuccess)
+    return fail(HODLR_ENOMEM, "device staging");
+  CK(cudaMemcpyAsync(d_stage.p, host_stage.data(), sizeof(double) * h->st_count,
+                     cudaMemcpyHostToDevice, s));
+  st = finish_from_staging(h, (const double*)d_stage.p, nullptr, nullptr, opts, s);
+  if (st != HODLR_OK) return st;
   *out = guard.release();
   return HODLR_OK;
 }
@@ -516,10 +515,31 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   cudaStream_t s = (cudaStream_t)stream;
   for (int c0 = 0; c0 < nrhs; c0 += h->max_nrhs) {
     const int nb = std::min(h->max_nrhs, nrhs - c0);
+    const bool last = c0 + h->max_nrhs >= nrhs;
     cudaError_t e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y,
-                                  h->d_partials, h->d_counters, s);
+                                  h->d_partials, h->d_counters, s,
+                                  (h->prof_on && last) ? h->prof_ev : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
   }
+  if (h->prof_on) h->prof_valid = true;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_profile(hodlr_t h, int32_t enable) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  if (enable && !h->prof_ev[0])
+    for (cudaEvent_t& e : h->prof_ev) CK(cudaEventCreate(&e));
+  h->prof_on = enable != 0;
+  h->prof_valid = false;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_profile_read(hodlr_t h, float* ms, int32_t count) {
+  if (!h || !ms || count < 2) return fail(HODLR_EINVAL, "null handle/ms or count < 2");
+  if (!h->prof_on || !h->prof_valid) return fail(HODLR_EINVAL, "no profiled call");
+  CK(cudaEventSynchronize(h->prof_ev[2]));
+  CK(cudaEventElapsedTime(&ms[0], h->prof_ev[0], h->prof_ev[1]));
+  CK(cudaEventElapsedTime(&ms[1], h->prof_ev[1], h->prof_ev[2]));
   return HODLR_OK;
 }
 

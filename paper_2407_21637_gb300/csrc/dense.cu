@@ -12,30 +12,6 @@ namespace {
 constexpr int kDenseThreads = 256;
 constexpr int kDenseCols = 8;  // right-hand sides per pass
 
-__device__ __forceinline__ double kernel_entry(const double* __restrict__ pts, int dim, int i, int j,
-                                               int kind, double c, double len2, double diag) {
-  if (kind == 3) {  // 1/(x_i - x_j), 1D; 0 at i == j plus diag
-    if (i == j) return diag;
-    return 1.0 / (pts[i] - pts[j]);
-  }
-  double r2 = 0.0;
-  for (int d = 0; d < dim; ++d) {
-    const double t = pts[(int64_t)i * dim + d] - pts[(int64_t)j * dim + d];
-    r2 = fma(t, t, r2);
-  }
-  double f;
-  if (kind == 1) {
-    f = exp(-r2 / len2);
-  } else if (i == j) {
-    // f(0) where it is finite, 0 for the singular kernels
-    f = c > 0.0 ? (kind == 0 ? 1.0 / c : log(c)) : 0.0;
-  } else {
-    const double r = sqrt(r2);
-    f = kind == 0 ? 1.0 / (r + c) : log(r + c);
-  }
-  return i == j ? f + diag : f;
-}
-
 __global__ void __launch_bounds__(kDenseThreads)
 dense_kernel_matvec_kernel(int n, int dim, const double* __restrict__ pts, int kind, double c,
                            double len2, double diag, int nrows, const int32_t* __restrict__ rows,

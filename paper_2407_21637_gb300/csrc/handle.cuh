@@ -1,0 +1,77 @@
+// Host-side handle of libhodlr and the import pipeline shared by
+// hodlr_import (caller-provided generators) and hodlr_build (generators
+// computed on the device).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "hodlr_internal.cuh"
+
+using hodlr::NodeDev;
+using hodlr::LeafDev;
+using hodlr::P1Item;
+using hodlr::P2Item;
+using hodlr::PackTask;
+using hodlr::HandleDev;
+
+struct hodlr_s {
+  std::vector<std::vector<std::pair<int, int>>> lv;  // cluster tree (row0, m) per level
+  int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
+  double eps = 0.0;
+  uint32_t avail = 0;
+  int device = 0;
+  std::vector<NodeDev> nodes;
+  std::vector<LeafDev> leaves;
+  std::vector<P1Item> p1;
+  std::vector<P2Item> p2;
+  std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
+  std::vector<int64_t> st_U, st_V, st_D; // staging offsets (elements)
+  int64_t st_count = 0;
+  hodlr_info_t info{};
+  int build_sketch_max = 0;          // largest sketch hodlr_build used
+  bool build_accuracy_short = false;  // some block hit the sketch cap
+  uint8_t* d_pool = nullptr;
+  size_t pool_bytes = 0;
+  NodeDev* d_nodes = nullptr;
+  LeafDev* d_leaves = nullptr;
+  P1Item* d_p1 = nullptr;
+  P2Item* d_p2 = nullptr;
+  void* d_Y = nullptr;
+  void* d_partials = nullptr;
+  unsigned* d_counters = nullptr;
+  size_t scratch_bytes = 0;
+  HandleDev hd{};
+  cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
+  bool prof_on = false, prof_valid = false;
+
+  ~hodlr_s() {
+    for (cudaEvent_t& e : prof_ev)
+      if (e) cudaEventDestroy(e);
+    cudaFree(d_pool);
+    cudaFree(d_nodes);
+    cudaFree(d_leaves);
+    cudaFree(d_p1);
+    cudaFree(d_p2);
+    cudaFree(d_Y);
+    cudaFree(d_partials);
+    cudaFree(d_counters);
+  }
+};
+
+namespace hodlr {
+
+hodlr_status set_error(hodlr_status s, const std::string& msg);
+hodlr_status set_cuda_error(cudaError_t e, const char* where);
+
+// Tree, leaves, nodes (ranks) and the fp64 staging layout; validates sizes.
+hodlr_status plan_layout(hodlr_s* h, int n, int depth, const int32_t* ranks, const hodlr_opts* opts);
+
+// From fp64 generators in the device staging (layout of plan_layout): the
+// precision rule, packing, work lists and scratch.  ``block_norm2`` (per node
+// q = block (k, i)) and ``leaf_norm2`` are the norms of the original matrix
+// when known (hodlr_build), else nullptr (norms of the factors are used).
+hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double* block_norm2,
+                                 const double* leaf_norm2, const hodlr_opts* opts, cudaStream_t s);
+
+}  // namespace hodlr

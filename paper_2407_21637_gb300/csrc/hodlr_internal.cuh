@@ -188,6 +188,32 @@ __device__ __forceinline__ void store1(uint8_t* base, int prec, double x) {
   }
 }
 
+// ---- kernel-matrix entries (eq. (4.1) and the synthetic workloads) ---------
+// A_ij = f(r_ij) + diag*delta_ij; at i == j, f is f(0) where finite, else 0.
+__device__ __forceinline__ double kernel_entry(const double* __restrict__ pts, int dim, int i, int j,
+                                               int kind, double c, double len2, double diag) {
+  if (kind == 3) {  // 1/(x_i - x_j), 1D; 0 at i == j plus diag
+    if (i == j) return diag;
+    return 1.0 / (pts[i] - pts[j]);
+  }
+  double r2 = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    const double t = pts[(int64_t)i * dim + d] - pts[(int64_t)j * dim + d];
+    r2 = fma(t, t, r2);
+  }
+  double f;
+  if (kind == 1) {
+    f = exp(-r2 / len2);
+  } else if (i == j) {
+    // f(0) where it is finite, 0 for the singular kernels
+    f = c > 0.0 ? (kind == 0 ? 1.0 / c : log(c)) : 0.0;
+  } else {
+    const double r = sqrt(r2);
+    f = kind == 0 ? 1.0 / (r + c) : log(r + c);
+  }
+  return i == j ? f + diag : f;
+}
+
 // ---- kernel launchers implemented in the .cu files -------------------------
 struct PackTask {          // one column of one generator or leaf
   int64_t src;             // element offset of (row 0, column c) in the fp64 staging
@@ -211,9 +237,11 @@ cudaError_t launch_pack(const double* staging, const PackTask* tasks, int ntasks
 cudaError_t launch_unpack(const uint8_t* pool, const PackTask* tasks, int ntasks,
                           double* staging, cudaStream_t s);
 
+// ev (may be null): three events recorded before phase 1, between the phases
+// and after phase 2.
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, void* Y, void* partials, unsigned* counters,
-                          cudaStream_t s);
+                          cudaStream_t s, cudaEvent_t* ev);
 
 cudaError_t launch_dense_kernel_matvec(int n, int dim, const double* pts, int kind, double c,
                                        double len2, double diag, int nrows, const int32_t* rows,

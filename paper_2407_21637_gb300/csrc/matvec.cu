@@ -278,12 +278,14 @@ phase2_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R,
 
 template <typename W, int CT>
 cudaError_t launch_ct(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb,
-                      W* Y, W* partials, unsigned* counters, cudaStream_t s) {
+                      W* Y, W* partials, unsigned* counters, cudaStream_t s, cudaEvent_t* ev) {
+  if (ev) cudaEventRecord(ev[0], s);
   if (hd.n_p1 > 0) {
     phase1_kernel<W, CT><<<hd.n_p1, kThreads, 0, s>>>(hd, X, ldx, nrhs, Y, partials, counters);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  if (ev) cudaEventRecord(ev[1], s);
   const size_t smem = phase2_smem_bytes<W, CT>(hd);
   static size_t smem_set = 48 * 1024;   // per instantiation: largest size opted in so far
   if (smem > smem_set) {
@@ -293,28 +295,29 @@ cudaError_t launch_ct(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W*
     smem_set = smem;
   }
   phase2_kernel<W, CT><<<hd.n_p2, kThreads, smem, s>>>(hd, X, ldx, nrhs, Y, B, ldb);
+  if (ev) cudaEventRecord(ev[2], s);
   return cudaGetLastError();
 }
 
 template <typename W>
 cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb,
-                     W* Y, W* partials, unsigned* counters, cudaStream_t s) {
-  if (nrhs == 1) return launch_ct<W, 1>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s);
-  if (nrhs == 2) return launch_ct<W, 2>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s);
-  if (nrhs <= 4) return launch_ct<W, 4>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s);
-  return launch_ct<W, 8>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s);
+                     W* Y, W* partials, unsigned* counters, cudaStream_t s, cudaEvent_t* ev) {
+  if (nrhs == 1) return launch_ct<W, 1>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
+  if (nrhs == 2) return launch_ct<W, 2>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
+  if (nrhs <= 4) return launch_ct<W, 4>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
+  return launch_ct<W, 8>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
 }
 
 }  // namespace
 
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, void* Y, void* partials, unsigned* counters,
-                          cudaStream_t s) {
+                          cudaStream_t s, cudaEvent_t* ev) {
   if (work == HODLR_FP64)
     return launch_w<double>(hd, nrhs, (const double*)X, ldx, (double*)B, ldb, (double*)Y,
-                            (double*)partials, counters, s);
+                            (double*)partials, counters, s, ev);
   return launch_w<float>(hd, nrhs, (const float*)X, ldx, (float*)B, ldb, (float*)Y,
-                         (float*)partials, counters, s);
+                         (float*)partials, counters, s, ev);
 }
 
 }  // namespace hodlr

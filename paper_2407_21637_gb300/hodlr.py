@@ -11,7 +11,7 @@ from typing import Sequence
 import numpy as np
 import torch
 
-from ._lib import PREC, PREC_NAME, Info, Opts, check, load
+from ._lib import PREC, PREC_NAME, BuildOpts, Info, Kernel, Opts, check, load
 
 _TORCH_DTYPE = {"fp64": torch.float64, "fp32": torch.float32}
 
@@ -84,6 +84,36 @@ class HodlrMatrix:
         del ku, kv, kd
         return cls(h, n, depth, work)
 
+    @classmethod
+    def build(cls, points: torch.Tensor, kind: int, depth: int, eps: float, c: float = 0.0,
+              len2: float = 1.0, diag: float = 0.0, work: str = "fp32",
+              tiers: Sequence[str] = ("fp64", "fp32", "bf16", "fp16", "e4m3"),
+              per_block: bool = False, max_nrhs: int = 64, sketch: int = 0, max_sketch: int = 0,
+              seed: int = 0, stream=None, allow_short: bool = False) -> "HodlrMatrix":
+        """hodlr_build: compress the kernel matrix of ``points`` ((n, dim) fp64
+        CUDA tensor, tree order) on the GPU (Algorithm 3.2 with a randomized
+        range finder) and store it in the adaptive-precision format."""
+        lib = load()
+        pts = points if points.dim() == 2 else points.view(-1, 1)
+        if pts.dtype != torch.float64 or not pts.is_cuda:
+            raise ValueError("points must be a float64 CUDA tensor")
+        pts = pts.contiguous()
+        n, dim = pts.shape
+        kern = Kernel(kind=int(kind), dim=int(dim), c=float(c), len2=float(len2), diag=float(diag))
+        mask = 0
+        for t in tiers:
+            mask |= 1 << PREC[t]
+        opts = Opts(eps=float(eps), work=PREC[work], tier_mask=mask, per_block=int(per_block),
+                    max_nrhs=int(max_nrhs))
+        bo = BuildOpts(sketch=int(sketch), max_sketch=int(max_sketch), seed=int(seed))
+        h = ctypes.c_void_p()
+        st = lib.hodlr_build(n, depth, ctypes.byref(kern), ctypes.c_void_p(pts.data_ptr()),
+                             ctypes.byref(opts), ctypes.byref(bo), _stream_ptr(stream), ctypes.byref(h))
+        if st == 7 and allow_short and h.value:
+            return cls(h, n, depth, work)
+        check(st, "hodlr_build")
+        return cls(h, n, depth, work)
+
     # ---- products -----------------------------------------------------
     def matvec(self, X: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """B = H X on the device (hodlr_matvec).  X: (n,) or (n, R) CUDA tensor of
@@ -114,6 +144,7 @@ class HodlrMatrix:
             "n": inf.n, "depth": inf.depth, "work": PREC_NAME[inf.work], "per_block": inf.per_block,
             "max_rank": inf.max_rank, "n_blocks": inf.n_blocks,
             "factor_bytes": inf.factor_bytes, "leaf_bytes": inf.leaf_bytes,
+            "u_bytes": inf.u_bytes, "v_bytes": inf.v_bytes,
             "scale_bytes": inf.scale_bytes, "device_bytes": inf.device_bytes,
             "bytes_per_tier": {PREC_NAME[p]: inf.bytes_per_tier[p] for p in range(6)},
             "norm2_all": inf.norm2_all,
@@ -121,6 +152,16 @@ class HodlrMatrix:
             "u_prime": [inf.u_prime[k] for k in range(d + 1)],
             "level_tier": [PREC_NAME.get(inf.level_tier[k], "?") if k else None for k in range(d + 1)],
         }
+
+    def profile(self, enable: bool = True):
+        """hodlr_profile: time each kernel of the following products with CUDA events."""
+        check(load().hodlr_profile(self._h, int(enable)), "hodlr_profile")
+
+    def profile_read(self):
+        """hodlr_profile_read: (phase-1 ms, phase-2 ms) of the last profiled product."""
+        ms = (ctypes.c_float * 2)()
+        check(load().hodlr_profile_read(self._h, ms, 2), "hodlr_profile_read")
+        return float(ms[0]), float(ms[1])
 
     def block_tiers(self):
         nn = (1 << (self.depth + 1)) - 2
