@@ -331,7 +331,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
 
   // ---- work lists ----
   int yoff = 0, poff = 0, sum_r_max = 0;
-  const int p1_leaves = std::max(1, 1024 / leaf_pm_max);  // leaves per phase-1 item
+  const int p1_leaves = std::min(kP1MaxLeaves, std::max(1, kP1Rows / leaf_pm_max));  // leaves per phase-1 item
   h->p1.clear();
   h->p2.clear();
   for (int k = 1; k <= depth; ++k) {
@@ -360,7 +360,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     int sr = 0;
     for (int k = 1; k <= depth; ++k) sr += h->nodes[node_index(k, l >> (depth - k))].rU;
     sum_r_max = std::max(sum_r_max, sr);
-    for (int t0 = 0; t0 < h->leaves[l].m; t0 += kTileRows) h->p2.push_back({l, t0});
+    for (int t0 = 0; t0 < h->leaves[l].m; t0 += kP2Rows) h->p2.push_back({l, t0});
   }
 
   // ---- descriptors and scratch on the device ----

@@ -23,6 +23,8 @@
 // hodlr_import, with the exact block norms of H.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <string>
 #include <memory>
 #include <vector>
 
@@ -227,7 +229,12 @@ __global__ void reduce_parts_kernel(BBlock* __restrict__ blocks, int nblk, const
 //   update  coef = sum of the block's partials in item order; X[:, j] -= X[:, :j] coef;
 //           R[:j, j] (+)= coef (first item only); ||X[:, j]||^2 partial per item
 //   (dot, update) twice, then
-//   norm    X[:, j] /= ||X[:, j]|| (0 if the norm is 0); R[j][j] = ||X[:, j]||.
+//   norm    X[:, j] /= ||X[:, j]||; R[j][j] = ||X[:, j]||.
+// A column whose remainder after the two projections is below 1e-12 of its
+// original length lies in the span of the previous columns to working
+// accuracy: it is set to zero (R[j][j] = 0) instead of normalising rounding
+// noise, which two passes cannot orthogonalise.  Zero columns of Q are
+// harmless for the range finder (the matching rows of Q^T A vanish).
 // Blocks with j >= s skip.  All sums have a fixed order: deterministic.
 constexpr int kPanelRows = 2048;
 
@@ -237,19 +244,19 @@ cgs_dot_kernel(const BBlock* __restrict__ blocks, const TItem* __restrict__ item
   __shared__ double red[kBT / kSmax][kSmax];
   const TItem it = items[blockIdx.x];
   const BBlock b = blocks[it.blk];
-  if (j >= b.s || j == 0) return;
+  if (j >= b.s) return;
   const int s = b.s;
   const int rows = side == 0 ? b.m : b.mc;
   const double* X = buf + (side == 0 ? b.yoff : b.boff);
   const int c = threadIdx.x % kSmax, g = threadIdx.x / kSmax;
   double acc = 0.0;
   const int rend = min(it.row0 + kPanelRows, rows);
-  if (c < j)
+  if (c <= j)
     for (int r = it.row0 + g; r < rend; r += kBT / kSmax)
       acc = fma(X[(int64_t)r * s + c], X[(int64_t)r * s + j], acc);
   red[g][c] = acc;
   __syncthreads();
-  if (g == 0 && c < j) {
+  if (g == 0 && c <= j) {
     double t = 0.0;
     for (int q = 0; q < kBT / kSmax; ++q) t += red[q][c];
     part[(int64_t)blockIdx.x * kSmax + c] = t;
@@ -271,9 +278,13 @@ cgs_update_kernel(const BBlock* __restrict__ blocks, const TItem* __restrict__ i
   double* X = buf + (side == 0 ? b.yoff : b.boff);
   double* R = mats + b.moff + rslot * kMat;
   const bool first = blockIdx.x == p0;
-  for (int c = threadIdx.x; c < j; c += kBT) {
+  for (int c = threadIdx.x; c <= j; c += kBT) {
     double t = 0.0;
     for (int q = 0; q < np; ++q) t += part[(int64_t)(p0 + q) * kSmax + c];
+    if (c == j) {   // self dot: the squared length before the projections (pass 0)
+      if (first && !second) mats[b.moff + kTmp * kMat + j] = t;
+      continue;
+    }
     coef[c] = t;
     if (first) R[c * kSmax + j] = second ? R[c * kSmax + j] + t : t;
   }
@@ -315,8 +326,10 @@ cgs_norm_kernel(const BBlock* __restrict__ blocks, const TItem* __restrict__ ite
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int q = 0; q < np; ++q) t += npart[p0 + q];
-    const double nr = sqrt(t);
-    s_inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    const double orig2 = mats[b.moff + kTmp * kMat + j];
+    const bool keep = t > 1e-24 * orig2 && t > 0.0;
+    const double nr = keep ? sqrt(t) : 0.0;
+    s_inv = keep ? 1.0 / nr : 0.0;
     if (blockIdx.x == p0) mats[b.moff + rslot * kMat + j * kSmax + j] = nr;
   }
   __syncthreads();
@@ -672,6 +685,8 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
     }
   int s = s0;
   bool accuracy_short = false;
+  double worst_ratio = 0.0;
+  std::string worst_msg;
   while (!pending.empty()) {
     auto R = std::make_unique<Round>();
     for (BBlock b : pending) {
@@ -688,7 +703,18 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
         pending.push_back(b);
         continue;
       }
-      if (b.retry) accuracy_short = true;
+      if (b.retry) {
+        const double ratio = b.resid2 / (opts->eps * opts->eps * b.norm2);
+        if (!accuracy_short || ratio > worst_ratio) {
+          worst_ratio = ratio;
+          char buf[256];
+          snprintf(buf, sizeof(buf),
+                   "block node %d (%d x %d) at sketch %d: sketch residual^2 = %.3e, eps^2 ||A_b||^2 = %.3e, "
+                   "||A_b||^2 = %.3e", b.q, b.m, b.mc, b.s, b.resid2, opts->eps * opts->eps * b.norm2, b.norm2);
+          worst_msg = buf;
+        }
+        accuracy_short = true;
+      }
       final_round[b.q] = ri;
       final_idx[b.q] = bi;
       block_norm2[b.q] = b.norm2;
@@ -748,6 +774,6 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
   h->build_accuracy_short = accuracy_short;
   *out = guard.release();
   if (accuracy_short)
-    return set_error(HODLR_EACCURACY, "some block needed a sketch larger than max_sketch; its rank is capped");
+    return set_error(HODLR_EACCURACY, "a block needed a sketch larger than max_sketch (its rank is capped); worst: " + worst_msg);
   return HODLR_OK;
 }

@@ -25,7 +25,9 @@
 namespace hodlr {
 
 constexpr int kRowPad = 16;          // padded leaf length multiple (elements)
-constexpr int kTileRows = 64;        // rows per product tile (phase 2)
+constexpr int kP2Rows = 32;          // rows per product tile (phase 2)
+constexpr int kP1Rows = 4096;        // padded rows per phase-1 work item (whole leaves)
+constexpr int kP1MaxLeaves = 256;    // leaves per phase-1 work item at most
 constexpr int kMaxLeaf = 1024;       // largest leaf supported by the product kernels
 constexpr int kPrecCount = 6;
 
@@ -55,7 +57,7 @@ struct P1Item {
   int32_t poff;                   // partial sums at rows [poff, poff + rV) of the partial buffer
 };
 
-// Phase-2 work item: rows [t0, t0 + kTileRows) of a leaf.
+// Phase-2 work item: rows [t0, t0 + kP2Rows) of a leaf.
 struct P2Item {
   int32_t leaf, t0;
 };

@@ -139,3 +139,25 @@ def test_build_is_deterministic():
         assert np.array_equal(a, b)
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("sketch", [16, 32, 64])
+def test_build_oversized_sketch_is_exact(sketch):
+    """A sketch far wider than the numerical rank (ranks 2-7 here) leaves
+    columns that lie in the span of the others to working accuracy; the
+    orthonormalisation must drop them, not amplify rounding noise."""
+    n, depth, eps = 4096, 4, 1e-6
+    spec = synth.KernelSpec(K.GAUSS, len2=0.01, diag=1e-2)
+    pts = synth.uniform_points_1d(n, 45)
+    A = K.kernel_matrix(pts, spec)
+    g = _gpu_build(pts, spec, depth, eps, "fp64", ("fp64",), sketch=sketch, max_sketch=64)
+    h = _as_oracle(g, n, depth)
+    for k in range(1, depth + 1):
+        for i, (s, m) in enumerate(h.levels[k]):
+            (s1, m1) = h.levels[k][i ^ 1]
+            blk = A[s:s + m, s1:s1 + m1]
+            U, Vs = h.U[k][i], h.V[k][i ^ 1]
+            assert np.linalg.norm(blk - U @ Vs.T) <= eps * np.linalg.norm(blk) * (1 + 1e-6)
+            assert U.shape[1] <= 10
+            assert np.linalg.norm(U.T @ U - np.eye(U.shape[1])) <= 1e-12
+    g.close()
