@@ -198,6 +198,31 @@ hodlr_status hodlr_export(hodlr_t h, double* const* U, double* const* V,
 hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, int32_t xb_prec, void* stream);
 
+/* hodlr_matvec_noalloc -- the same product as hodlr_matvec, for callers that
+ * cannot allocate device memory when they multiply: for example a process
+ * whose device memory is already fully reserved by another allocator (a
+ * framework's caching allocator or a pre-partitioned pool), or code on a
+ * latency-critical path that must not enter the driver's allocator.  The
+ * paper has no counterpart; this is a library convenience.
+ *
+ * It allocates nothing (no cudaMalloc, cudaFree or allocating library call)
+ * and does not use the handle's own scratch: its scratch is one 4 MiB device
+ * array inside this library, which every GPU that loads the library holds
+ * until the process exits.  Arguments and results are those of hodlr_matvec
+ * (same kernels, same summation order, bitwise the same B).  Right-hand sides
+ * are processed in batches that fit the array; a matrix whose per-column
+ * scratch (its V^T X results and partial sums, about 8 bytes per rank column
+ * per node and work item) does not fit at all is rejected with HODLR_EINVAL.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on every handle shares the array and the array keeps the last
+ * call's contents: the call clears what must start at zero itself, and calls
+ * that overlap in time on the GPU (different streams, threads or handles)
+ * race on the array and must be serialised by the caller. */
+hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
+                                  void* B, int64_t ldb, int32_t xb_prec, void* stream);
+
 /* hodlr_profile -- enable (1) or disable (0) CUDA-event timing of the
  * kernels launched by the following hodlr_matvec calls on this handle (events
  * are recorded on the call's stream around each kernel of its last column

@@ -63,6 +63,8 @@ SIGNATURES = {
     "hodlr_export": (ctypes.c_int, [_P, _DP, _DP, _DP, _P]),
     "hodlr_matvec": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                     ctypes.c_int32, _P]),
+    "hodlr_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
+                                            ctypes.c_int32, _P]),
     "hodlr_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
     "hodlr_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "hodlr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
