@@ -229,9 +229,10 @@ hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void* X, int64_
  * batch; recording costs a few microseconds of host time per call). */
 hodlr_status hodlr_profile(hodlr_t h, int32_t enable);
 
-/* hodlr_profile_read -- device time in ms of each kernel of the last
- * profiled hodlr_matvec: ms[0] = phase 1 (V^T X, all levels), ms[1] = phase 2
- * (leaf products and U Y).  count >= 2.  Waits for that call's events.
+/* hodlr_profile_read -- device time in ms of the last profiled hodlr_matvec
+ * launch: ms[0] = the product kernel (all of Algorithm 3.3 in one persistent
+ * launch), ms[1] = time after it up to the end of the call's work (0 when the
+ * product is one launch).  count >= 2.  Waits for that call's events.
  * HODLR_EINVAL when profiling is off or nothing was profiled yet. */
 hodlr_status hodlr_profile_read(hodlr_t h, float* ms, int32_t count);
 

@@ -260,144 +260,301 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     }
   }
 
-  // ---- pool layout ----
-  size_t pool = 0;
+  // ---- formats and scales of every generator ----
   const int ebw = prec_bytes(h->work);
-  h->tasks.clear();
-  for (int k = 1; k <= depth; ++k) {
+  std::vector<double> sU(nnodes, 1.0), sV(nnodes, 1.0);
+  for (int k = 1; k <= depth; ++k)
     for (int i = 0; i < (1 << k); ++i) {
       const int q = node_index(k, i);
       NodeDev& nd = h->nodes[q];
       nd.tierU = block_tier[q];
       nd.tierV = block_tier[node_index(k, i ^ 1)];
-      const double sU = pow2_scale(amax[nnodes + q], nd.tierU);
-      const double sV = pow2_scale(amax[q], nd.tierV);
-      nd.invsU = 1.0 / sU;
-      nd.invsV = 1.0 / sV;
-      pool = align_up(pool, 256);
-      nd.offU = (int64_t)pool;
-      pool += (size_t)nd.rU * nd.pm * prec_bytes(nd.tierU);
-      pool = align_up(pool, 256);
-      nd.offV = (int64_t)pool;
-      pool += (size_t)nd.rV * nd.pm * prec_bytes(nd.tierV);
+      sU[q] = pow2_scale(amax[nnodes + q], nd.tierU);
+      sV[q] = pow2_scale(amax[q], nd.tierV);
+      nd.invsU = 1.0 / sU[q];
+      nd.invsV = 1.0 / sV[q];
       inf.max_rank = std::max(inf.max_rank, nd.rU);
       inf.factor_bytes += (int64_t)nd.m * (nd.rU * prec_bytes(nd.tierU) + nd.rV * prec_bytes(nd.tierV));
       inf.u_bytes += (int64_t)nd.m * nd.rU * prec_bytes(nd.tierU);
       inf.v_bytes += (int64_t)nd.m * nd.rV * prec_bytes(nd.tierV);
       inf.bytes_per_tier[nd.tierU] += (int64_t)nd.m * nd.rU * prec_bytes(nd.tierU);
       inf.bytes_per_tier[nd.tierV] += (int64_t)nd.m * nd.rV * prec_bytes(nd.tierV);
-      if (sU != 1.0 && nd.rU) inf.scale_bytes += 8;
-      if (sV != 1.0 && nd.rV) inf.scale_bytes += 8;
-      // pack tasks: one per generator column and leaf segment (padded row space)
-      const int span = 1 << (depth - k);
+      if (sU[q] != 1.0 && nd.rU) inf.scale_bytes += 8;
+      if (sV[q] != 1.0 && nd.rV) inf.scale_bytes += 8;
+    }
+  for (const LeafDev& lf : h->leaves) inf.leaf_bytes += (int64_t)lf.m * lf.m * ebw;
+
+  // ---- pool: V columns per node (phase 1), then one region per leaf tile ----
+  size_t pool = 0;
+  h->tasks.clear();
+  for (int k = 1; k <= depth; ++k) {
+    const int span = 1 << (depth - k);
+    for (int i = 0; i < (1 << k); ++i) {
+      const int q = node_index(k, i);
+      NodeDev& nd = h->nodes[q];
+      pool = align_up(pool, 256);
+      nd.offV = (int64_t)pool;
+      const int ebv = prec_bytes(nd.tierV);
+      pool += (size_t)nd.rV * nd.pm * ebv;
       for (int l = i * span; l < (i + 1) * span; ++l) {
         const LeafDev& lf = h->leaves[l];
         const int rel = lf.row0 - nd.row0, prel = lf.prow0 - nd.prow0;
-        for (int c = 0; c < nd.rU; ++c) {
-          const int ebu = prec_bytes(nd.tierU);
-          h->tasks.push_back({h->st_U[q] + (int64_t)rel * nd.rU + c, nd.rU, lf.m, lf.pm,
-                              nd.offU + ((int64_t)c * nd.pm + prel) * ebu, nd.tierU, 0, sU});
-        }
-        for (int c = 0; c < nd.rV; ++c) {
-          const int ebv = prec_bytes(nd.tierV);
+        for (int c = 0; c < nd.rV; ++c)
           h->tasks.push_back({h->st_V[q] + (int64_t)rel * nd.rV + c, nd.rV, lf.m, lf.pm,
-                              nd.offV + ((int64_t)c * nd.pm + prel) * ebv, nd.tierV, 0, sV});
-        }
+                              nd.offV + ((int64_t)c * nd.pm + prel) * ebv, nd.tierV, 0, sV[q]});
       }
     }
   }
+  // tiles
+  h->p2.clear();
+  std::vector<std::pair<int64_t, uint32_t>> headers;   // (byte offset in pool, word)
+  int max_nq = 0, max_region = 0;
+  std::vector<int> leaf_nq(nleaves, 0), leaf_yrow(nleaves, 0);
+  int yrows = 0;
   for (int l = 0; l < nleaves; ++l) {
-    LeafDev& lf = h->leaves[l];
-    pool = align_up(pool, 256);
-    lf.offD = (int64_t)pool;
-    pool += (size_t)lf.m * lf.pm * ebw;
-    inf.leaf_bytes += (int64_t)lf.m * lf.m * ebw;
-    for (int j = 0; j < lf.m; ++j)
-      h->tasks.push_back({h->st_D[l] + j, lf.m, lf.m, lf.pm, lf.offD + (int64_t)j * lf.pm * ebw,
-                          h->work, 0, 1.0});
+    const LeafDev& lf = h->leaves[l];
+    // the leaf's U columns: ancestors level 1..depth, columns 0..rU-1
+    std::vector<int> anc(depth + 1, 0);
+    int nq = 0;
+    for (int k = 1; k <= depth; ++k) {
+      anc[k] = node_index(k, l >> (depth - k));
+      nq += h->nodes[anc[k]].rU;
+    }
+    leaf_nq[l] = nq;
+    leaf_yrow[l] = yrows;
+    yrows += (int)align_up(nq, 4);               // 16-byte aligned blocks in fp32 and fp64
+    max_nq = std::max(max_nq, nq);
+    const int hbytes = (int)align_up((size_t)8 * depth, 16);   // one header entry per level
+    const int mp = (int)align_up(lf.m, 4);                // D row length (zero padded)
+    const int dbytes = mp * kTileRows * ebw;
+    // byte offset of each level's U segment inside the U area
+    std::vector<int> useg(depth + 2, 0);
+    for (int k = 1; k <= depth; ++k) {
+      const NodeDev& a = h->nodes[anc[k]];
+      useg[k + 1] = useg[k] + (int)align_up((size_t)a.rU * kTileRows * prec_bytes(a.tierU), 16);
+    }
+    const int ubytes = useg[depth + 1];
+    const int region = hbytes + ubytes + dbytes;
+    max_region = std::max(max_region, dbytes);
+    for (int t0 = 0; t0 < lf.m; t0 += kTileRows) {
+      pool = align_up(pool, 128);
+      P2Tile tl;
+      memset(&tl, 0, sizeof(tl));
+      tl.off = (int64_t)pool;
+      tl.bytes = region;
+      tl.hbytes = hbytes;
+      tl.ubytes = ubytes;
+      tl.dbytes = dbytes;
+      tl.m = lf.m;
+      tl.rows = std::min(kTileRows, lf.m - t0);
+      tl.row0 = lf.row0 + t0;
+      tl.xrow0 = lf.row0;
+      tl.nq = nq;
+      tl.yrow = leaf_yrow[l];
+      h->p2.push_back(tl);
+      // header, two words per level k = 1..depth: byte offset of the level's
+      // U block inside the U area; rank | format << 16
+      for (int k = 1; k <= depth; ++k) {
+        const NodeDev& a = h->nodes[anc[k]];
+        headers.push_back({tl.off + 8 * (k - 1), (uint32_t)useg[k]});
+        headers.push_back({tl.off + 8 * (k - 1) + 4, (uint32_t)a.rU | ((uint32_t)a.tierU << 16)});
+      }
+      // D[t0:t0+32, j] for every column j (row-major, row stride mp)
+      for (int j = 0; j < lf.m; ++j)
+        h->tasks.push_back({h->st_D[l] + (int64_t)t0 * lf.m + j, lf.m, tl.rows, kTileRows,
+                            tl.off + hbytes + ubytes + (int64_t)j * ebw, h->work, mp * ebw, 1.0});
+      // U_a[rows of this tile, c] for every ancestor a and column c (column
+      // by column: 32 consecutive rows per column)
+      for (int k = 1; k <= depth; ++k) {
+        const int q = anc[k];
+        const NodeDev& a = h->nodes[q];
+        const int eb = prec_bytes(a.tierU);
+        const int rel = lf.row0 - a.row0 + t0;
+        for (int c = 0; c < a.rU; ++c)
+          h->tasks.push_back({h->st_U[q] + (int64_t)rel * a.rU + c, a.rU, tl.rows, kTileRows,
+                              tl.off + hbytes + useg[k] + (int64_t)c * kTileRows * eb, a.tierU, 0, sU[q]});
+      }
+      pool += region;
+    }
   }
   pool = align_up(std::max<size_t>(pool, 256), 256);
   h->pool_bytes = pool;
   if (cudaMalloc((void**)&h->d_pool, pool) != cudaSuccess) return fail(HODLR_ENOMEM, "factor pool");
   CK(cudaMemsetAsync(h->d_pool, 0, pool, s));
   {
-    DevBuf d_tasks;
+    DevBuf d_tasks, d_hoff, d_hval;
     CK(cudaMalloc(&d_tasks.p, std::max<size_t>(h->tasks.size(), 1) * sizeof(PackTask)));
     CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask),
                        cudaMemcpyHostToDevice, s));
     CK(launch_pack(d_stage, (const PackTask*)d_tasks.p, (int)h->tasks.size(), h->d_pool, s));
+    std::vector<int64_t> hoff(headers.size());
+    std::vector<uint32_t> hval(headers.size());
+    for (size_t e = 0; e < headers.size(); ++e) { hoff[e] = headers[e].first; hval[e] = headers[e].second; }
+    CK(cudaMalloc(&d_hoff.p, std::max<size_t>(hoff.size(), 1) * sizeof(int64_t)));
+    CK(cudaMalloc(&d_hval.p, std::max<size_t>(hval.size(), 1) * sizeof(uint32_t)));
+    CK(cudaMemcpyAsync(d_hoff.p, hoff.data(), hoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(d_hval.p, hval.data(), hval.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CK(launch_put_words(h->d_pool, (const int64_t*)d_hoff.p, (const uint32_t*)d_hval.p, (int64_t)hoff.size(), s));
     CK(cudaStreamSynchronize(s));
   }
 
-  // ---- work lists ----
-  int yoff = 0, poff = 0, sum_r_max = 0;
-  const int p1_leaves = std::min(kP1MaxLeaves, std::max(1, kP1Rows / leaf_pm_max));  // leaves per phase-1 item
-  h->p1.clear();
-  h->p2.clear();
+  // ---- phase-1 work items and the scatter table of the gathered Y ----
+  // yscat: for node j (level k), one entry per leaf L below the sibling of j:
+  // the gathered-Y row of Y_j[0] in L's block.
+  std::vector<int32_t> yscat;
+  std::vector<int> yscat0(nnodes, 0), nyscat(nnodes, 0);
+  for (int k = 1; k <= depth; ++k) {
+    const int span = 1 << (depth - k);
+    for (int j = 0; j < (1 << k); ++j) {
+      const int q = node_index(k, j);
+      yscat0[q] = (int)yscat.size();
+      const int sib = j ^ 1;
+      for (int L = sib * span; L < (sib + 1) * span; ++L) {
+        int q0 = 0;   // U columns of L's ancestors above level k
+        for (int kk = 1; kk < k; ++kk) q0 += h->nodes[node_index(kk, L >> (depth - kk))].rU;
+        yscat.push_back(leaf_yrow[L] + q0);
+      }
+      nyscat[q] = (int)yscat.size() - yscat0[q];
+    }
+  }
+  // V chunks: runs of whole leaves (or pieces of a leaf) of one node whose
+  // rV column segments fit one shared-memory stage of the product kernel.
+  int poff = 0, chunk_xrows_max = 0;
+  h->vch.clear();
+  h->nred.clear();
   for (int k = 1; k <= depth; ++k) {
     const int span = 1 << (depth - k);
     for (int i = 0; i < (1 << k); ++i) {
       const int q = node_index(k, i);
-      NodeDev& nd = h->nodes[q];
-      nd.yoff = yoff;
-      yoff += nd.rV;
+      const NodeDev& nd = h->nodes[q];
       if (nd.rV == 0) continue;
-      const int nitems = (span + p1_leaves - 1) / p1_leaves;
-      for (int t = 0; t < nitems; ++t) {
-        P1Item it;
-        it.node = q;
-        it.leaf0 = i * span + t * p1_leaves;
-        it.nleaf = std::min(p1_leaves, span - t * p1_leaves);
-        it.item_in_node = t;
-        it.nitems = nitems;
-        it.poff = poff;
-        poff += nd.rV;
-        h->p1.push_back(it);
+      const int eb = prec_bytes(nd.tierV);
+      // at most kChunkRows padded rows (one warp of the product takes a chunk)
+      const int cap = kChunkRows;
+      NodeRed red;
+      memset(&red, 0, sizeof(red));
+      // Y_node is only ever multiplied by U of the sibling: fold both
+      // power-of-two scales (exact) into the gathered Y
+      red.invs = nd.invsV * h->nodes[node_index(k, i ^ 1)].invsU;
+      red.rV = nd.rV;
+      red.poff0 = poff;
+      red.yscat0 = yscat0[q];
+      red.nyscat = nyscat[q];
+      VChunk ch;
+      bool open = false;
+      auto close_chunk = [&]() {
+        if (!open) return;
+        ch.bytes = ch.rows * eb;
+        int xend = ch.xrow0;
+        for (int e = 0; e < ch.nseg; ++e)
+          if (ch.seg[e].m > 0) xend = std::max(xend, ch.seg[e].row0 + ch.seg[e].m);
+        ch.xrows = xend - ch.xrow0;
+        chunk_xrows_max = std::max(chunk_xrows_max, ch.xrows);
+        h->vch.push_back(ch);
+        poff += nd.rV;                           // one partial per chunk
+        red.nparts += 1;
+        open = false;
+      };
+      for (int l = i * span; l < (i + 1) * span; ++l) {
+        const LeafDev& lf = h->leaves[l];
+        for (int o = 0; o < lf.pm;) {
+          if (open && (ch.rows >= cap || ch.nseg == kP1Segs)) close_chunk();
+          if (!open) {
+            memset(&ch, 0, sizeof(ch));
+            const int p0 = lf.prow0 - nd.prow0 + o;
+            ch.off = nd.offV + (int64_t)p0 * eb;
+            ch.colbytes = nd.pm * eb;
+            ch.rV = nd.rV;
+            ch.node = (int)h->nred.size();
+            ch.tier = nd.tierV;
+            ch.poff = poff;
+            ch.xrow0 = lf.row0 + o;
+            open = true;
+          }
+          const int len = std::min(lf.pm - o, cap - ch.rows);
+          P1Seg& sg = ch.seg[ch.nseg++];
+          sg.row0 = lf.row0 + o;
+          sg.m = std::max(0, std::min(len, lf.m - o));
+          sg.prel = ch.rows;
+          ch.rows += len;
+          o += len;
+        }
       }
+      close_chunk();
+      h->nred.push_back(red);
     }
-  }
-  for (int l = 0; l < nleaves; ++l) {
-    int sr = 0;
-    for (int k = 1; k <= depth; ++k) sr += h->nodes[node_index(k, l >> (depth - k))].rU;
-    sum_r_max = std::max(sum_r_max, sr);
-    for (int t0 = 0; t0 < h->leaves[l].m; t0 += kP2Rows) h->p2.push_back({l, t0});
   }
 
   // ---- descriptors and scratch on the device ----
   hodlr_status st;
   if ((st = upload(h->nodes, &h->d_nodes)) != HODLR_OK) return st;
   if ((st = upload(h->leaves, &h->d_leaves)) != HODLR_OK) return st;
-  if ((st = upload(h->p1, &h->d_p1)) != HODLR_OK) return st;
+  if ((st = upload(h->vch, &h->d_vch)) != HODLR_OK) return st;
+  if ((st = upload(h->nred, &h->d_nred)) != HODLR_OK) return st;
+  // reduction items, nodes with the most partials first (they take longest)
+  std::vector<int2> ritems;
+  for (size_t j = 0; j < h->nred.size(); ++j)
+    for (int a = 0; a < h->nred[j].rV; ++a) ritems.push_back(make_int2((int)j, a));
+  std::stable_sort(ritems.begin(), ritems.end(), [&](const int2& x, const int2& y) {
+    return h->nred[x.x].nparts > h->nred[y.x].nparts;
+  });
+  if ((st = upload(ritems, &h->d_ritems)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
-  const size_t yb = (size_t)std::max(yoff, 1) * h->max_nrhs * ebw;
+  if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
+  // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
+  // for the rounded-up tile copies
+  const size_t yb = ((size_t)std::max(yrows, 1) * h->max_nrhs + 4) * ebw;
   const size_t pb = (size_t)std::max(poff, 1) * h->max_nrhs * ebw;
   if (cudaMalloc(&h->d_Y, yb) != cudaSuccess) return fail(HODLR_ENOMEM, "Y scratch");
   if (cudaMalloc(&h->d_partials, pb) != cudaSuccess) return fail(HODLR_ENOMEM, "partials scratch");
-  if (cudaMalloc((void**)&h->d_counters, sizeof(unsigned) * std::max(nnodes, 1)) != cudaSuccess)
-    return fail(HODLR_ENOMEM, "counters");
-  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned) * std::max(nnodes, 1), s));
+  // grid counter (starts at zero and only grows)
+  const size_t sync_bytes = kSyncHeadBytes;
+  if (cudaMalloc((void**)&h->d_sync, sync_bytes) != cudaSuccess) return fail(HODLR_ENOMEM, "grid counter");
+  if (cudaMalloc((void**)&h->d_err, sizeof(int)) != cudaSuccess) return fail(HODLR_ENOMEM, "error word");
+  CK(cudaMemsetAsync(h->d_sync, 0, sync_bytes, s));
+  h->sync_base = 0;
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(h->d_Y, 0, yb, s));
   CK(cudaStreamSynchronize(s));
-  h->scratch_bytes = yb + pb + sizeof(unsigned) * std::max(nnodes, 1);
+  h->scratch_bytes = yb + pb + sync_bytes;
 
   HandleDev& hd = h->hd;
+  memset(&hd, 0, sizeof(hd));
   hd.nodes = h->d_nodes;
   hd.leaves = h->d_leaves;
-  hd.p1 = h->d_p1;
+  hd.vch = h->d_vch;
+  hd.nred = h->d_nred;
   hd.p2 = h->d_p2;
+  hd.yscat = h->d_yscat;
+  hd.ritems = h->d_ritems;
+  hd.n_ritems = (int)ritems.size();
   hd.pool = h->d_pool;
+  hd.err = h->d_err;
   hd.n = n;
   hd.depth = depth;
   hd.n_nodes = nnodes;
   hd.n_leaves = nleaves;
-  hd.n_p1 = (int)h->p1.size();
+  hd.n_vch = (int)h->vch.size();
+  hd.n_nred = (int)h->nred.size();
   hd.n_p2 = (int)h->p2.size();
-  hd.y_rows = yoff;
+  hd.chunk_xrows_max = chunk_xrows_max;
+  hd.y_rows = yrows;
   hd.p_rows = poff;
-  hd.sum_r_max = sum_r_max;
+  hd.max_nq = max_nq;
+  // a stage holds the leaf-block part of one tile
+  hd.stage_bytes = (int)align_up((size_t)std::max(max_region, 16), 128);
   hd.leaf_pm_max = leaf_pm_max;
+  hd.x_aligned = 1;
+  for (const LeafDev& lf : h->leaves) {
+    hd.leaf_m_max = std::max(hd.leaf_m_max, lf.m);
+    if (lf.row0 % 4 || lf.m % 4) hd.x_aligned = 0;
+  }
+  const int mb = matvec_max_batch(hd, h->work);
+  if (mb < 1) return fail(HODLR_EINVAL, "leaf blocks too large for the product's shared-memory stages; increase depth");
+  h->batch = std::min(h->max_nrhs, mb);
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
-                               h->leaves.size() * sizeof(LeafDev) + h->p1.size() * sizeof(P1Item) +
-                               h->p2.size() * sizeof(P2Item));
+                               h->leaves.size() * sizeof(LeafDev) + h->vch.size() * sizeof(VChunk) +
+                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
   return HODLR_OK;
 }
 
@@ -513,12 +670,13 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   const size_t span_x = ((size_t)(h->n - 1) * ldx + nrhs) * es, span_b = ((size_t)(h->n - 1) * ldb + nrhs) * es;
   if (!(xb + span_x <= bb || bb + span_b <= xb)) return fail(HODLR_EINVAL, "X and B overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int c0 = 0; c0 < nrhs; c0 += h->max_nrhs) {
-    const int nb = std::min(h->max_nrhs, nrhs - c0);
-    const bool last = c0 + h->max_nrhs >= nrhs;
+  for (int c0 = 0; c0 < nrhs; c0 += h->batch) {
+    const int nb = std::min(h->batch, nrhs - c0);
+    const bool last = c0 + h->batch >= nrhs;
     cudaError_t e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y,
-                                  h->d_partials, h->d_counters, s,
+                                  h->d_partials, h->d_sync, h->sync_base, s,
                                   (h->prof_on && last) ? h->prof_ev : nullptr);
+    h->sync_base += matvec_sync_step(h->hd);
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
   }
   if (h->prof_on) h->prof_valid = true;

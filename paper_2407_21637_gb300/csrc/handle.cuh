@@ -10,21 +10,25 @@
 
 using hodlr::NodeDev;
 using hodlr::LeafDev;
-using hodlr::P1Item;
-using hodlr::P2Item;
+using hodlr::VChunk;
+using hodlr::NodeRed;
+using hodlr::P1Seg;
+using hodlr::P2Tile;
 using hodlr::PackTask;
 using hodlr::HandleDev;
 
 struct hodlr_s {
   std::vector<std::vector<std::pair<int, int>>> lv;  // cluster tree (row0, m) per level
   int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
+  int batch = 64;                      // right-hand sides per product launch
   double eps = 0.0;
   uint32_t avail = 0;
   int device = 0;
   std::vector<NodeDev> nodes;
   std::vector<LeafDev> leaves;
-  std::vector<P1Item> p1;
-  std::vector<P2Item> p2;
+  std::vector<VChunk> vch;
+  std::vector<NodeRed> nred;
+  std::vector<P2Tile> p2;
   std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
   std::vector<int64_t> st_U, st_V, st_D; // staging offsets (elements)
   int64_t st_count = 0;
@@ -35,11 +39,16 @@ struct hodlr_s {
   size_t pool_bytes = 0;
   NodeDev* d_nodes = nullptr;
   LeafDev* d_leaves = nullptr;
-  P1Item* d_p1 = nullptr;
-  P2Item* d_p2 = nullptr;
+  VChunk* d_vch = nullptr;
+  NodeRed* d_nred = nullptr;
+  int2* d_ritems = nullptr;
+  P2Tile* d_p2 = nullptr;
+  int32_t* d_yscat = nullptr;
+  int* d_err = nullptr;
   void* d_Y = nullptr;
   void* d_partials = nullptr;
-  unsigned* d_counters = nullptr;
+  unsigned long long* d_sync = nullptr;   // grid barrier counter of the product kernel
+  unsigned long long sync_base = 0;       // its value before the next launch
   size_t scratch_bytes = 0;
   HandleDev hd{};
   cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
@@ -51,11 +60,15 @@ struct hodlr_s {
     cudaFree(d_pool);
     cudaFree(d_nodes);
     cudaFree(d_leaves);
-    cudaFree(d_p1);
+    cudaFree(d_vch);
+    cudaFree(d_nred);
+    cudaFree(d_ritems);
     cudaFree(d_p2);
+    cudaFree(d_yscat);
+    cudaFree(d_err);
     cudaFree(d_Y);
     cudaFree(d_partials);
-    cudaFree(d_counters);
+    cudaFree(d_sync);
   }
 };
 

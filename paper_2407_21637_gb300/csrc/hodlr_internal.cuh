@@ -25,9 +25,6 @@
 namespace hodlr {
 
 constexpr int kRowPad = 16;          // padded leaf length multiple (elements)
-constexpr int kP2Rows = 32;          // rows per product tile (phase 2)
-constexpr int kP1Rows = 4096;        // padded rows per phase-1 work item (whole leaves)
-constexpr int kP1MaxLeaves = 256;    // leaves per phase-1 work item at most
 constexpr int kMaxLeaf = 1024;       // largest leaf supported by the product kernels
 constexpr int kPrecCount = 6;
 
@@ -50,30 +47,89 @@ struct LeafDev {
   int32_t pad_;
 };
 
-// Phase-1 work item: V_node^T X over the leaves [leaf0, leaf0 + nleaf) of node.
-struct P1Item {
-  int32_t node, leaf0, nleaf;
-  int32_t item_in_node, nitems;   // position among the node's items
-  int32_t poff;                   // partial sums at rows [poff, poff + rV) of the partial buffer
+constexpr int kP1Segs = 16;          // leaf segments per V chunk at most (inline)
+constexpr int kTileRows = 32;        // rows per product tile
+constexpr int kChunkRows = 256;      // padded rows per V chunk at most
+constexpr int kConsumerWarps = 16;   // consumer warps of the product kernel
+
+// Bytes of the product's sync buffer (a 64-bit grid counter, padded).
+constexpr int kSyncHeadBytes = 256;
+
+// One leaf (or piece of a leaf) of a V chunk.
+struct P1Seg {
+  int32_t row0, m;                // first real row and valid rows of the segment
+  int32_t prel;                   // padded offset of the segment inside the chunk
+  int32_t pad_;
 };
 
-// Phase-2 work item: rows [t0, t0 + kP2Rows) of a leaf.
-struct P2Item {
-  int32_t leaf, t0;
+// V chunk: padded rows [p0, p0 + rows) of all rV columns of V_node (column c
+// at byte offset off + c * colbytes of the pool).  The warp that takes it
+// writes its part of V_node^T X to partial rows [poff, poff + rV).
+struct VChunk {
+  int64_t off;                    // byte offset of column 0 at padded row p0
+  int32_t colbytes;               // bytes between columns in the pool (pm * eb)
+  int32_t bytes;                  // bytes per column segment (rows * eb, multiple of 16)
+  int32_t rows, node;             // padded rows; index of the node's NodeRed
+  int32_t rV, tier, poff, nseg;   // rank, format, partial rows, segments
+  int32_t xrow0, xrows;           // real rows covered (X rows xrow0 .. xrow0 + xrows)
+  P1Seg seg[kP1Segs];
+};
+
+// Final reduction of one node: Y_node = invs * sum of its chunk partials
+// (chunk order), written to its gathered-Y targets.  The rows of every node
+// are reduction items (node, row) spread over the whole grid.
+struct NodeRed {
+  double invs;                    // 1/s of V_node times 1/s of U of the node's sibling
+  int32_t rV, poff0, nparts;      // part p has partial rows poff0 + p * rV
+  int32_t yscat0, nyscat;         // targets of Y_node in the gathered Y (see HandleDev)
+  int32_t pad_;
+};
+
+// Product tile: rows [t0, t0 + kTileRows) of a leaf.  Its data is one
+// contiguous region of the pool: a header of two words per level (byte
+// offset of the level's U block in the U area; rank | format << 16), the
+// ancestors' U rows for these 32 rows (level by level, column by column, 32
+// rows per column, each level in its own format), then the leaf block
+// D[t0:t0+32, :] row by row (row length m rounded up to 4, zero padded).
+// The D part streams through shared memory (it does not depend on V^T X);
+// header and U are read directly once Y is complete.
+struct P2Tile {
+  int64_t off;                    // byte offset of the region in the pool
+  int32_t bytes, hbytes, dbytes;  // region, header and D bytes (multiples of 16)
+  int32_t m;                      // leaf rows = D columns
+  int32_t rows;                   // valid rows in the tile (<= 32)
+  int32_t row0;                   // first real row of the tile
+  int32_t xrow0;                  // first real row of the leaf (row of X for column 0)
+  int32_t nq;                     // U columns (sum of the ancestors' ranks)
+  int32_t yrow;                   // first row of the leaf's block in the gathered Y
+  int32_t ubytes;                 // U bytes (multiple of 16); D starts at hbytes + ubytes
 };
 
 // Device-resident description of a handle (passed by value to kernels).
+// The gathered Y: for every leaf, the rows Y_{a_k ^ 1} (k = 1..depth) its
+// tiles need, in the order of the tile's U columns, one block per leaf
+// (row-major, R values per row).  Phase 1 writes each Y_j into the blocks of
+// all leaves below the sibling of j: yscat[yscat0 .. yscat0 + nyscat) hold
+// the target rows.
 struct HandleDev {
   const NodeDev* nodes;
   const LeafDev* leaves;
-  const P1Item* p1;
-  const P2Item* p2;
+  const VChunk* vch;
+  const NodeRed* nred;
+  const P2Tile* p2;
+  const int32_t* yscat;
+  const int2* ritems;             // reduction items: (NodeRed index, row of Y_node), all nodes
   const uint8_t* pool;
+  int* err;                       // device error word (bounded waits that gave up)
   int32_t n, depth, n_nodes, n_leaves;
-  int32_t n_p1, n_p2;
-  int32_t y_rows, p_rows;         // rows (rank units) of the Y and partial buffers
-  int32_t sum_r_max;              // max over leaves of sum_k rU(ancestor_k)
+  int32_t n_vch, n_nred, n_p2, n_ritems;
+  int32_t chunk_xrows_max;        // largest real-row span of a V chunk
+  int32_t y_rows, p_rows;         // rows of the gathered Y and of the partial buffer
+  int32_t max_nq;                 // largest U column count of a tile
+  int32_t stage_bytes;            // largest tile region (multiple of 128)
   int32_t leaf_pm_max;
+  int32_t leaf_m_max;             // largest leaf
+  int32_t x_aligned;              // every leaf starts and ends on a multiple of 4 rows
 };
 
 __host__ __device__ inline int node_index(int k, int i) { return (1 << k) - 2 + i; }
@@ -221,9 +277,9 @@ struct PackTask {          // one column of one generator or leaf
   int64_t src;             // element offset of (row 0, column c) in the fp64 staging
   int32_t src_stride;      // elements between consecutive rows in the staging
   int32_t m, pm;           // rows, padded rows
-  int64_t dst;             // byte offset of the column in the pool
+  int64_t dst;             // byte offset of (row 0, column c) in the pool
   int32_t prec;
-  int32_t pad_;
+  int32_t dst_stride;      // bytes between consecutive rows in the pool (0: the element size)
   double scale;            // multiply before rounding (power of two)
 };
 
@@ -236,14 +292,29 @@ cudaError_t launch_norms(const double* staging, const NormTask* tasks, int ntask
                          double* sumsq, double* amax, cudaStream_t s);
 cudaError_t launch_pack(const double* staging, const PackTask* tasks, int ntasks,
                         uint8_t* pool, cudaStream_t s);
+cudaError_t launch_put_words(uint8_t* pool, const int64_t* off, const uint32_t* val, int64_t count,
+                             cudaStream_t s);
 cudaError_t launch_unpack(const uint8_t* pool, const PackTask* tasks, int ntasks,
                           double* staging, cudaStream_t s);
 
-// ev (may be null): three events recorded before phase 1, between the phases
-// and after phase 2.
+// One product launch (nrhs right-hand sides).  Y: gathered Y (y_rows * nrhs
+// values + 4 of slack), partials: p_rows * nrhs values, sync: kSyncHeadBytes
+// holding a 64-bit grid counter whose value is `sync_base` when the launch
+// starts (the launch adds matvec_sync_step to it).
+// ev (may be null): three events, recorded before the launch and twice after.
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
-                          void* B, int64_t ldb, void* Y, void* partials, unsigned* counters,
+                          void* B, int64_t ldb, void* Y, void* partials,
+                          unsigned long long* sync, unsigned long long sync_base,
                           cudaStream_t s, cudaEvent_t* ev);
+// The grid size launch_matvec uses.
+int matvec_grid(const HandleDev& hd);
+// How far one launch advances the grid barrier counter (sync_base of the
+// next launch on the same counter = this launch's + matvec_sync_step).
+unsigned long long matvec_sync_step(const HandleDev& hd);
+
+// Widest batch of right-hand sides one product launch accepts (shared-memory
+// stages of phase 2); 0 when even one column does not fit.
+int matvec_max_batch(const HandleDev& hd, int work);
 
 cudaError_t launch_dense_kernel_matvec(int n, int dim, const double* pts, int kind, double c,
                                        double len2, double diag, int nrows, const int32_t* rows,

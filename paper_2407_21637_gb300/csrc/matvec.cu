@@ -1,47 +1,122 @@
-// HODLR_MATVEC (Algorithm 3.3) on sm_103a CUDA cores.
+// HODLR_MATVEC (Algorithm 3.3) on sm_103a.
 //
 // Algorithm 3.3 walks the levels and adds U_{2i-1}(V_{2i}^T x_{2i}) and
 // U_{2i}(V_{2i-1}^T x_{2i-1}) into b, then the leaf products D_i x_i.  Here
-// the level loop is flattened into two data-parallel kernels:
+// the level loop is flattened into one persistent kernel (one CTA per SM,
+// cooperative launch so that all CTAs are co-resident) with three stages per
+// CTA:
 //
-//  phase 1  Y_j = V_j^T X[I_j] for every node j of every level: one work item
-//           per node and group of leaves (up to 4096 rows); partial sums per
-//           item, and the last item of a node to finish adds the partials in
-//           item order, so the result does not depend on scheduling;
-//  phase 2  for every 32-row tile of a leaf i:
-//           B[rows] = D_i X[I_i] + sum_k U_{a_k}[rows] Y_{a_k ^ 1}
-//           where a_k is the level-k ancestor of leaf i; each output row is
-//           written once, by one CTA, with a fixed summation order.
+//  phase A  Y_j = V_j^T X[I_j] for every node j of every level, in chunks of
+//           up to 512 rows; each Y_j is written into the gathered-Y block of
+//           every leaf below the sibling of j;
+//  pass 1   for every 32-row tile of a leaf i: D_i[rows, :] X[I_i], which
+//           does not depend on phase A;
+//  pass 2   for every tile: B[rows] = (pass 1) + sum_k U_{a_k}[rows, :]
+//           Y_{a_k ^ 1}, a_k the level-k ancestor of leaf i.
 //
-// Phase 2 is launched with programmatic dependent launch: its CTAs start
-// while phase 1 runs, stream their leaf block D_i (the bulk of the bytes)
-// and only then wait for phase 1 (griddepcontrol.wait) before reading Y.
-// Phase 1 releases its dependents as soon as it starts.
-//
-// Both kernels stream their factor bytes once (V in phase 1, U and D in
-// phase 2).  Threads run along rows: a thread owns 4 consecutive rows and
-// loads the 4 entries of a generator column (16 bytes in fp32) at a time,
-// converting the block's storage format to the working precision on the fly.
+// Each output row is written once, with a fixed summation order, so the
+// product is bitwise reproducible.  A producer warp per CTA streams the V
+// chunks, the tiles' leaf blocks and then the tiles' U rows and gathered-Y
+// blocks into a ring of shared-memory stages with bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier); sixteen consumer warps
+// multiply out of shared memory.  Only the producer waits for the other CTAs
+// (a grid counter that every CTA increments after phase A), just before it
+// copies the first gathered-Y block, so phase A of the slowest CTA overlaps
+// pass 1 everywhere.  Every wait gives up after two seconds; a wait that
+// gives up records an error code in the handle's error word and the CTA
+// drains the copies it issued and returns.
+#include <algorithm>
+#include <type_traits>
+
 #include "hodlr_internal.cuh"
 
 namespace hodlr {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kRankTile = 8;
-constexpr int kP2Lanes = kP2Rows / 4;              // threads per 4-row column segment
-constexpr int kP2Groups = kThreads / kP2Lanes;     // reduction groups over the columns
+constexpr int kCWarps = kConsumerWarps;       // consumer warps of the product kernel
+constexpr int kCThreads = 32 * kCWarps;
+constexpr int kRedWarps = 4;                  // node-reduction warps
+constexpr int kP2Threads = kCThreads + 32 + 32 * kRedWarps;   // consumers, producer, reducers
+constexpr int kMaxStages = 6;
+constexpr int kMaxColsLane = 16;              // right-hand sides per lane and step of pass 2
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // every wait gives up after 2 s
 
 template <typename W> struct WorkPrec;
 template <> struct WorkPrec<float> { static constexpr int value = HODLR_FP32; };
 template <> struct WorkPrec<double> { static constexpr int value = HODLR_FP64; };
 
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+// ---- PTX helpers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// One test of the phase; a thread whose phase is not complete is suspended
+// in hardware until it completes or about kSuspendNs pass (no busy polling
+// of shared memory by waiting warps).
+constexpr uint32_t kSuspendNs = 1000000;
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: polls for a short while (the common case: the phase
+// completes within microseconds), then sleeps in try_wait; false (and the
+// error word set) if the phase has not completed within kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (int k = 0; k < 4096; ++k)
+    if (mbar_test_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
+  atomicExch(err, code);
+  return false;
+}
+// Bulk asynchronous copy global -> shared (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 
 template <typename W>
 __device__ __forceinline__ W warp_sum(W v) {
@@ -50,333 +125,694 @@ __device__ __forceinline__ W warp_sum(W v) {
   return v;
 }
 
-// Dynamic shared memory of phase 2: the rank-column tables first (8-byte
-// aligned), then the working-precision arrays from a 16-byte boundary.
-__host__ __device__ inline size_t phase2_w_offset(int sum_r_max) {
-  return ((size_t)sum_r_max * (sizeof(int64_t) + sizeof(int)) + 15) / 16 * 16;
+// ---- the product kernel ----------------------------------------------------
+// Phase A: every V chunk of this CTA -> its part of V_node^T X, summed over
+//          the CTA in a fixed order.  A node held by one chunk is finished
+//          on the spot (Y_node written to its gathered-Y targets); for a
+//          node of several chunks each chunk leaves a partial and the CTA
+//          that completes the last one adds them in chunk order.  Then the
+//          CTA arrives at the grid counter (without waiting).
+// Pass 1:  every tile of this CTA -> D[rows, :] X[I_i] (needs no Y), kept
+//          in shared memory (or in B when it does not fit).
+// Pass 2:  every tile of this CTA -> B[rows] = pass-1 result +
+//          U[rows, :] Yg[leaf].
+// The producer warp streams V chunks, the tiles' D parts, and, once the grid
+// counter shows that every CTA has finished phase A, the tiles' U parts with
+// their gathered-Y blocks, through one ring of shared-memory stages.  Only
+// the producer waits for the grid; the consumers never do.
+//
+// Lane layout: LC lanes across right-hand-side columns (CPL consecutive
+// columns each) and LK = 32 / LC lanes across the summation index, so that a
+// warp-wide load of X, Y or a factor touches LK consecutive rows of up to
+// LC * CPL consecutive columns.  Each lane sums its share of the index in
+// order, then the LK partial sums are added by a fixed butterfly.
+
+template <int LC, int CPL>
+struct Lanes {
+  static constexpr int LK = 32 / LC;            // lanes across the summation index
+  static constexpr int BW = LC * CPL;           // columns per pass
+  static constexpr int RTA = BW >= 32 ? 4 : 8;  // V columns per phase-A pass
+};
+
+// CPL consecutive values of a row (8- or 16-byte aligned when CPL = 2).
+template <typename W, int CPL>
+__device__ __forceinline__ void load_cols(const W* p, bool global, W (&v)[CPL]) {
+  if constexpr (CPL == 1) {
+    v[0] = global ? __ldg(p) : *p;
+  } else if constexpr (sizeof(W) == 4) {
+    const float2 t = global ? __ldg(reinterpret_cast<const float2*>(p)) : *reinterpret_cast<const float2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+    const double2 t = global ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  }
 }
-
-template <typename W, int CT>
-size_t phase2_smem_bytes(const HandleDev& hd) {
-  return phase2_w_offset(hd.sum_r_max) +
-         ((size_t)hd.leaf_pm_max * CT + (size_t)hd.sum_r_max * CT + (size_t)kWarps * kP2Rows * CT) *
-             sizeof(W);
-}
-
-// ---- phase 1: Y = V^T X ----------------------------------------------------
-template <typename W, int CT>
-__global__ void __launch_bounds__(kThreads)
-phase1_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R,
-              W* __restrict__ Y, W* __restrict__ partials, unsigned* __restrict__ counters) {
-  pdl_launch_dependents();
-  __shared__ W s_red[kWarps][kRankTile * CT];
-  __shared__ int s_pref[kP1MaxLeaves + 1];   // prefix sums of 4-row groups per leaf
-  __shared__ int s_last;
-  const P1Item it = hd.p1[blockIdx.x];
-  const NodeDev nd = hd.nodes[it.node];
-  const int rV = nd.rV;
-  const int eb = prec_bytes(nd.tierV);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    int t = 0;
-    for (int q = 0; q < it.nleaf; ++q) {
-      s_pref[q] = t;
-      t += hd.leaves[it.leaf0 + q].pm / 4;
-    }
-    s_pref[it.nleaf] = t;
-  }
-  __syncthreads();
-  const int ngroups = s_pref[it.nleaf];
-
-  for (int c0 = 0; c0 < R; c0 += CT) {
-    const int nc = min(CT, R - c0);
-    for (int r0 = 0; r0 < rV; r0 += kRankTile) {
-      const int nr = min(kRankTile, rV - r0);
-      W acc[kRankTile][CT];
-#pragma unroll
-      for (int c = 0; c < kRankTile; ++c)
-#pragma unroll
-        for (int j = 0; j < CT; ++j) acc[c][j] = (W)0;
-
-      int li = 0;
-      for (int gq = threadIdx.x; gq < ngroups; gq += kThreads) {
-        while (gq >= s_pref[li + 1]) ++li;           // groups are visited in increasing order
-        const LeafDev lf = hd.leaves[it.leaf0 + li];
-        const int p = 4 * (gq - s_pref[li]);          // padded row within the leaf
-        W xv[4][CT];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const bool ok = p + q < lf.m;
-          const W* xr = X + (int64_t)(lf.row0 + p + q) * ldx + c0;
-#pragma unroll
-          for (int j = 0; j < CT; ++j) xv[q][j] = (ok && j < nc) ? xr[j] : (W)0;
-        }
-        const uint8_t* vb = hd.pool + nd.offV + ((int64_t)r0 * nd.pm + (lf.prow0 - nd.prow0) + p) * eb;
-        Vec4<W> v[kRankTile];
-#pragma unroll
-        for (int c = 0; c < kRankTile; ++c)
-          if (c < nr) v[c] = load4<W>(vb + (int64_t)c * nd.pm * eb, nd.tierV);
-#pragma unroll
-        for (int c = 0; c < kRankTile; ++c) {
-          if (c < nr) {
-#pragma unroll
-            for (int j = 0; j < CT; ++j) {
-              W a = acc[c][j];
-              a = fma(v[c].x, xv[0][j], a);
-              a = fma(v[c].y, xv[1][j], a);
-              a = fma(v[c].z, xv[2][j], a);
-              a = fma(v[c].w, xv[3][j], a);
-              acc[c][j] = a;
-            }
-          }
-        }
-      }
-      // CTA reduction: warps, then the warp partials in warp order.
-#pragma unroll
-      for (int c = 0; c < kRankTile; ++c) {
-        if (c < nr) {
-#pragma unroll
-          for (int j = 0; j < CT; ++j) {
-            W v = warp_sum(acc[c][j]);
-            if (lane == 0) s_red[warp][c * CT + j] = v;
-          }
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x < nr * CT) {
-        const int c = threadIdx.x / CT, j = threadIdx.x % CT;
-        W s = (W)0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += s_red[w][threadIdx.x];
-        if (j < nc) partials[(int64_t)(it.poff + r0 + c) * R + c0 + j] = s;
-      }
-      __syncthreads();
-    }
-  }
-
-  // The last item of the node to finish adds the node's partials in item
-  // order (classic threadfence reduction; nothing waits on anything).
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned prev = atomicAdd(&counters[it.node], 1u);
-    s_last = prev == (unsigned)(it.nitems - 1);
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
-    const int first = blockIdx.x - it.item_in_node;
-    const W invs = (W)nd.invsV;
-    for (int e = threadIdx.x; e < rV * R; e += kThreads) {
-      const int c = e / R, j = e - c * R;
-      W s = (W)0;
-      for (int q = 0; q < it.nitems; ++q) {
-        const int poff = hd.p1[first + q].poff;
-        s += __ldcg(partials + (int64_t)(poff + c) * R + j);
-      }
-      Y[(int64_t)(nd.yoff + c) * R + j] = s * invs;
-    }
-    if (threadIdx.x == 0) counters[it.node] = 0u;
+template <typename W, int CPL>
+__device__ __forceinline__ void store_cols(W* p, const W (&v)[CPL]) {
+  if constexpr (CPL == 1) {
+    *p = v[0];
+  } else if constexpr (sizeof(W) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
   }
 }
 
-// ---- phase 2: B = D X + sum_k U Y ------------------------------------------
-template <typename W, int CT>
-__global__ void __launch_bounds__(kThreads)
-phase2_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R,
-              const W* __restrict__ Y, W* __restrict__ B, int64_t ldb) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  int64_t* qoff = reinterpret_cast<int64_t*>(smem);                // [sum_r_max]
-  int* qprec = reinterpret_cast<int*>(qoff + hd.sum_r_max);        // [sum_r_max]
-  W* Zx = reinterpret_cast<W*>(smem + phase2_w_offset(hd.sum_r_max));  // [leaf_pm_max][CT]
-  W* Zy = Zx + (size_t)hd.leaf_pm_max * CT;                        // [sum_r_max][CT]
-  W* red = Zy + (size_t)hd.sum_r_max * CT;                         // [kWarps][kP2Rows][CT]
-  __shared__ int s_anc[HODLR_MAX_DEPTH + 1];
-  __shared__ int s_q0[HODLR_MAX_DEPTH + 2];
+// ---- explicit shared-memory accesses (addresses in the shared window) ----
+// The hot loops address shared memory through these so that every access is
+// a shared-memory instruction, whatever the compiler can prove about a
+// pointer (a generic access that may go to global memory is much slower).
+__device__ __forceinline__ float sld_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double sld_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t sld_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint16_t sld_u16(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint16_t sld_u8(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+template <typename W>
+__device__ __forceinline__ W sld(uint32_t a) {
+  if constexpr (sizeof(W) == 4) return sld_f32(a);
+  else return sld_f64(a);
+}
+template <typename W>
+__device__ __forceinline__ void sst(uint32_t a, W v) {
+  if constexpr (sizeof(W) == 4) asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  else asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+// CPL consecutive values of W (8- or 16-byte aligned when CPL = 2)
+template <typename W, int CPL>
+__device__ __forceinline__ void sld_cols(uint32_t a, W (&v)[CPL]) {
+  if constexpr (CPL == 1) {
+    v[0] = sld<W>(a);
+  } else if constexpr (sizeof(W) == 4) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
+  } else {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[0]), "=d"(v[1]) : "r"(a));
+  }
+}
+template <typename W, int CPL>
+__device__ __forceinline__ void sst_cols(uint32_t a, const W (&v)[CPL]) {
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) sst<W>(a + j * (uint32_t)sizeof(W), v[j]);
+}
+// four consecutive fp32 values (16-byte aligned)
+__device__ __forceinline__ float4 sld_v4f32(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+// one element of storage format P (compile time), decoded into W
+template <typename W, int P>
+__device__ __forceinline__ W sld_fmt(uint32_t a) {
+  if constexpr (P == HODLR_FP64) {
+    return (W)sld_f64(a);
+  } else if constexpr (P == HODLR_FP32) {
+    return (W)sld_f32(a);
+  } else if constexpr (P == HODLR_FP16) {
+    return (W)__half2float(__ushort_as_half(sld_u16(a)));
+  } else if constexpr (P == HODLR_BF16) {
+    return (W)__uint_as_float(((uint32_t)sld_u16(a)) << 16);
+  } else {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)sld_u8(a), P == HODLR_E4M3 ? __NV_E4M3 : __NV_E5M2);
+    return (W)__half2float(*reinterpret_cast<__half*>(&h));
+  }
+}
 
-  constexpr int wprec = WorkPrec<W>::value;
+__device__ __forceinline__ void bar_consumers() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kCThreads) : "memory");
+}
+// Bounded wait until the grid counter reaches target (acquire).
+__device__ __forceinline__ bool grid_wait(unsigned long long* counter, unsigned long long target, int* err) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(counter) : "memory");
+    if (v >= target) return true;
+    if (global_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, 5);
+      return false;
+    }
+    __nanosleep(64);
+  }
+}
+
+// One element of storage format P (compile time) from global memory, in W.
+template <typename W, int P>
+__device__ __forceinline__ W gld_fmt(const uint8_t* p) {
+  if constexpr (P == HODLR_FP64) {
+    return (W)__ldg(reinterpret_cast<const double*>(p));
+  } else if constexpr (P == HODLR_FP32) {
+    return (W)__ldg(reinterpret_cast<const float*>(p));
+  } else if constexpr (P == HODLR_FP16) {
+    return (W)__half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+  } else if constexpr (P == HODLR_BF16) {
+    return (W)__uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+  } else {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)__ldg(reinterpret_cast<const unsigned char*>(p)),
+                                           P == HODLR_E4M3 ? __NV_E4M3 : __NV_E5M2);
+    return (W)__half2float(*reinterpret_cast<__half*>(&h));
+  }
+}
+
+template <typename W, int LC, int CPL>
+__global__ void __launch_bounds__(kP2Threads, 1)
+matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W* __restrict__ Yg,
+              W* __restrict__ partials, W* __restrict__ B, int64_t ldb, unsigned long long* sync,
+              unsigned long long sync_base, int nstages, int xstage_bytes, int res_smem) {
+  using L = Lanes<LC, CPL>;
+  constexpr int LK = L::LK, BW = L::BW, RTA = L::RTA;
+  extern __shared__ __align__(128) uint8_t smem[];
   constexpr int ebw = sizeof(W);
-  const P2Item it = hd.p2[blockIdx.x];
-  const LeafDev lf = hd.leaves[it.leaf];
-  const int g = threadIdx.x / kP2Lanes, l = threadIdx.x % kP2Lanes;
-  const int rowbase = it.t0 + 4 * l;                  // leaf-local first row of this thread
-  const bool active = rowbase < lf.pm;
-  const int depth = hd.depth;
+  const int G = gridDim.x;
+  const int ntiles = hd.n_p2 > (int)blockIdx.x ? (hd.n_p2 - (int)blockIdx.x + G - 1) / G : 0;   // this CTA's tiles
+  const int stage_bytes = hd.stage_bytes;
+  uint8_t* stages = smem;                                               // [S][stage_bytes]
+  uint8_t* xstages = smem + (size_t)nstages * stage_bytes;              // [S][xstage_bytes] (may be 0)
+  W* res = reinterpret_cast<W*>(xstages + (size_t)nstages * xstage_bytes);   // pass-1 results (if res_smem)
+  const size_t res_bytes = res_smem ? ((size_t)ntiles * kTileRows * R * ebw + 127) / 128 * 128 : 0;
+  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(res) + res_bytes);
+  uint64_t* empty = full + kMaxStages;
+  uint64_t* wbarA = empty + kMaxStages;                                 // [kCWarps] pass-2 copies
+  P2Tile* s_tile = reinterpret_cast<P2Tile*>(wbarA + kCWarps);          // [S]
 
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    int q = 0;
-    for (int k = 1; k <= depth; ++k) {
-      const int a = node_index(k, it.leaf >> (depth - k));
-      s_anc[k] = a;
-      s_q0[k] = q;
-      q += hd.nodes[a].rU;
+    for (int s = 0; s < nstages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kCWarps);
     }
-    s_q0[depth + 1] = q;
+    for (int w = 0; w < kCWarps; ++w) mbar_init(&wbarA[w], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int totq = s_q0[depth + 1];
-  // per rank column: byte offset of (tile row 0) in U's column, and its format
-  for (int k = 1; k <= depth; ++k) {
-    const NodeDev a = hd.nodes[s_anc[k]];
-    const int eb = prec_bytes(a.tierU);
-    const int64_t base = a.offU + (int64_t)(lf.prow0 - a.prow0 + it.t0) * eb;
-    for (int c = threadIdx.x; c < a.rU; c += kThreads) {
-      qoff[s_q0[k] + c] = base + (int64_t)c * a.pm * eb;
-      qprec[s_q0[k] + c] = a.tierU;
+
+  if (warp > kCWarps) {
+    // ================= reducers =================
+    // After every CTA's phase A (first stage of the grid counter), the rows
+    // of every node: Y_node[a, :] = invs * sum of its chunk partials (each
+    // lane sums the partials lane, lane + 32, ... in order, then a fixed
+    // butterfly), written to the node's gathered-Y targets.  Then the
+    // second stage of the grid counter.
+    const int rw = warp - kCWarps - 1;
+    if (hd.n_ritems > 0) {
+      if (lane == 0) grid_wait(sync, sync_base + (unsigned long long)G, hd.err);
+      __syncwarp();
+      for (int it = blockIdx.x * kRedWarps + rw; it < hd.n_ritems; it += G * kRedWarps) {
+        const int2 ri = __ldg(hd.ritems + it);
+        const NodeRed* nrp = hd.nred + ri.x;
+        const int P = __ldg(&nrp->nparts), rV = __ldg(&nrp->rV), poff0 = __ldg(&nrp->poff0);
+        const int y0 = __ldg(&nrp->yscat0), ny = __ldg(&nrp->nyscat);
+        const W invs = (W)__ldg(&nrp->invs);
+        const W* pp = partials + (int64_t)(poff0 + ri.y) * R;
+        for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
+          const int nc = min(kMaxColsLane, R - c0);
+          W acc[kMaxColsLane];
+#pragma unroll
+          for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+          for (int q = lane; q < P; q += 32) {
+            const W* row = pp + (int64_t)q * rV * R + c0;
+            W v[kMaxColsLane];
+#pragma unroll
+            for (int j = 0; j < kMaxColsLane; ++j) v[j] = j < nc ? __ldcg(row + j) : (W)0;
+#pragma unroll
+            for (int j = 0; j < kMaxColsLane; ++j) acc[j] += v[j];
+          }
+#pragma unroll
+          for (int j = 0; j < kMaxColsLane; ++j) acc[j] = warp_sum(acc[j]) * invs;
+          for (int t = lane; t < ny; t += 32) {
+            W* dst = Yg + (int64_t)(__ldg(hd.yscat + y0 + t) + ri.y) * R + c0;
+#pragma unroll
+            for (int j = 0; j < kMaxColsLane; ++j)
+              if (j < nc) dst[j] = acc[j];
+          }
+        }
+      }
+      __threadfence();
+    }
+    asm volatile("bar.sync 2, %0;" ::"r"(32 * kRedWarps) : "memory");
+    if (rw == 0 && lane == 0) atomicAdd(sync, 1ull);
+    return;
+  }
+
+  if (warp == kCWarps) {
+    // ================= producer: the leaf blocks of this CTA's tiles =================
+    if (lane != 0) return;
+    int i = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < hd.n_p2; tile += G, ++i) {
+      const int s = i % nstages;
+      if (i >= nstages && !(ok = mbar_wait(&empty[s], ((i / nstages) - 1) & 1, hd.err, 1))) break;
+      const P2Tile t = hd.p2[tile];
+      s_tile[s] = t;
+      const uint32_t xbytes = xstage_bytes ? (uint32_t)t.m * R * ebw : 0u;
+      mbar_arrive_expect_tx(&full[s], (uint32_t)t.dbytes + xbytes);
+      bulk_g2s(stages + (size_t)s * stage_bytes, hd.pool + t.off + t.hbytes + t.ubytes, (uint32_t)t.dbytes,
+               &full[s]);
+      if (xbytes) bulk_g2s(xstages + (size_t)s * xstage_bytes, X + (int64_t)t.xrow0 * R, xbytes, &full[s]);
+    }
+    if (!ok) {
+      // a wait gave up: let the copies already issued land before the CTA exits
+      for (int j = (i > nstages ? i - nstages : 0); j < i; ++j)
+        mbar_wait(&full[j % nstages], (j / nstages) & 1, hd.err, 3);
+    }
+    return;
+  }
+
+  // ================= consumers (warps 0 .. kCWarps-1) =================
+  const int tid = threadIdx.x;
+  const int kl = lane / LC, cl = lane - (lane / LC) * LC;   // lane = kl * LC + cl
+  bool alive = true;
+
+  // ---- phase A: every warp of the grid takes V chunks alone, reading V and
+  //      X directly (a chunk is at most kChunkRows rows of one node) ----
+  for (int c = blockIdx.x * kCWarps + warp; c < hd.n_vch; c += G * kCWarps) {
+    const VChunk& ch = hd.vch[c];
+    const int rV = __ldg(&ch.rV), poff = __ldg(&ch.poff), nseg = __ldg(&ch.nseg), tier = __ldg(&ch.tier);
+    const int colbytes = __ldg(&ch.colbytes);
+    const uint8_t* vbase = hd.pool + __ldg(&ch.off);
+    for (int c0 = 0; c0 < R; c0 += BW) {
+      const int col = c0 + cl * CPL;
+      const bool cok = col < R;
+      const int kcol = cok ? col : 0;   // lanes past the last column read column 0 and drop it
+      for (int r0 = 0; r0 < rV; r0 += RTA) {
+        W acc[RTA][CPL];
+#pragma unroll
+        for (int a = 0; a < RTA; ++a)
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) acc[a][j] = (W)0;
+        auto run = [&](auto tc) {
+          constexpr int TIER = decltype(tc)::value;
+          constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+          for (int li = 0; li < nseg; ++li) {
+            const int srow0 = __ldg(&ch.seg[li].row0), sm = __ldg(&ch.seg[li].m), sprel = __ldg(&ch.seg[li].prel);
+            const W* xgr = X + (int64_t)srow0 * ldx + kcol;
+            const uint8_t* vrow = vbase + (int64_t)r0 * colbytes + (int64_t)sprel * eb;
+#pragma unroll 4
+            for (int pl = kl; pl < sm; pl += LK) {
+              W xv[CPL];
+              load_cols<W, CPL>(xgr + (int64_t)pl * ldx, true, xv);
+              const uint8_t* vp = vrow + (int64_t)pl * eb;
+#pragma unroll
+              for (int a = 0; a < RTA; ++a) {
+                if (r0 + a < rV) {
+                  const W v = gld_fmt<W, TIER>(vp + (int64_t)a * colbytes);
+#pragma unroll
+                  for (int j = 0; j < CPL; ++j) acc[a][j] = fma(v, xv[j], acc[a][j]);
+                }
+              }
+            }
+          }
+        };
+        switch (tier) {
+          case HODLR_FP64: run(std::integral_constant<int, HODLR_FP64>{}); break;
+          case HODLR_FP32: run(std::integral_constant<int, HODLR_FP32>{}); break;
+          case HODLR_FP16: run(std::integral_constant<int, HODLR_FP16>{}); break;
+          case HODLR_BF16: run(std::integral_constant<int, HODLR_BF16>{}); break;
+          case HODLR_E4M3: run(std::integral_constant<int, HODLR_E4M3>{}); break;
+          default: run(std::integral_constant<int, HODLR_E5M2>{}); break;
+        }
+        // lanes of one column: fixed butterfly; the chunk's partial
+#pragma unroll
+        for (int a = 0; a < RTA; ++a)
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+            for (int o = LC; o < 32; o <<= 1) acc[a][j] += __shfl_xor_sync(0xffffffffu, acc[a][j], o);
+          }
+        if (kl == 0 && cok) {
+#pragma unroll
+          for (int a = 0; a < RTA; ++a)
+            if (r0 + a < rV) store_cols<W, CPL>(partials + (int64_t)(poff + r0 + a) * R + col, acc[a]);
+        }
+      }
+    }
+  }
+  // ---- first stage of the grid counter: this CTA's partials are written ----
+  __threadfence();
+  bar_consumers();
+  if (tid == 0) atomicAdd(sync, 1ull);
+
+  // ---- pass 1: D[rows, :] X[I_i] for every tile; warp w owns rows 2w, 2w + 1 ----
+  static_assert(kTileRows == 2 * kCWarps, "two rows per consumer warp");
+  static_assert(kTileRows == 32, "one lane per tile row in pass 2");
+  {
+    const int ra = 2 * warp, rb = 2 * warp + 1;
+    for (int tl = 0; tl < ntiles; ++tl) {
+      const int s = tl % nstages;
+      if (!mbar_wait(&full[s], (tl / nstages) & 1, hd.err, 4)) {
+        alive = false;
+        break;
+      }
+      const P2Tile t = s_tile[s];
+      const uint32_t st_a = smem_u32(stages + (size_t)s * stage_bytes);
+      const uint32_t xs_a = smem_u32(xstages + (size_t)s * xstage_bytes);
+      // pass-1 results of tile tl, column by column (32 rows per column)
+      const uint32_t res_t = smem_u32(res) + (uint32_t)((size_t)tl * kTileRows * R * ebw);
+      const int mp = (t.m + 3) & ~3;   // D row length
+      const uint32_t da = st_a + (uint32_t)(ra * mp * ebw), db = da + (uint32_t)(mp * ebw);
+      for (int c0 = 0; c0 < R; c0 += BW) {
+        const int col = c0 + cl * CPL;
+        const bool cok = col < R;
+        const int kcol = cok ? col : 0;   // lanes past the last column read column 0 and drop it
+        W acc0[CPL], acc1[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) acc0[j] = acc1[j] = (W)0;
+        bool done = false;
+        if constexpr (LC == 1 && CPL == 1 && sizeof(W) == 4) {
+          if (xstage_bytes) {
+            // one right-hand side, X staged (m is a multiple of 4): four
+            // consecutive columns of D per lane and step
+            for (int k = 4 * lane; k < t.m; k += 128) {
+              const float4 x4 = sld_v4f32(xs_a + (uint32_t)(k * 4));
+              const float4 a4 = sld_v4f32(da + (uint32_t)(k * 4));
+              const float4 b4 = sld_v4f32(db + (uint32_t)(k * 4));
+              acc0[0] = fmaf(a4.x, x4.x, acc0[0]);
+              acc1[0] = fmaf(b4.x, x4.x, acc1[0]);
+              acc0[0] = fmaf(a4.y, x4.y, acc0[0]);
+              acc1[0] = fmaf(b4.y, x4.y, acc1[0]);
+              acc0[0] = fmaf(a4.z, x4.z, acc0[0]);
+              acc1[0] = fmaf(b4.z, x4.z, acc1[0]);
+              acc0[0] = fmaf(a4.w, x4.w, acc0[0]);
+              acc1[0] = fmaf(b4.w, x4.w, acc1[0]);
+            }
+            done = true;
+          }
+        }
+        if (!done) {
+          if (xstage_bytes) {
+#pragma unroll 4
+            for (int k = kl; k < t.m; k += LK) {
+              W xv[CPL];
+              sld_cols<W, CPL>(xs_a + (uint32_t)((k * R + kcol) * ebw), xv);
+              const W d0 = sld<W>(da + (uint32_t)(k * ebw)), d1 = sld<W>(db + (uint32_t)(k * ebw));
+#pragma unroll
+              for (int j = 0; j < CPL; ++j) {
+                acc0[j] = fma(d0, xv[j], acc0[j]);
+                acc1[j] = fma(d1, xv[j], acc1[j]);
+              }
+            }
+          } else {
+            const W* xg = X + (int64_t)t.xrow0 * ldx + kcol;
+#pragma unroll 4
+            for (int k = kl; k < t.m; k += LK) {
+              W xv[CPL];
+              load_cols<W, CPL>(xg + (int64_t)k * ldx, true, xv);
+              const W d0 = sld<W>(da + (uint32_t)(k * ebw)), d1 = sld<W>(db + (uint32_t)(k * ebw));
+#pragma unroll
+              for (int j = 0; j < CPL; ++j) {
+                acc0[j] = fma(d0, xv[j], acc0[j]);
+                acc1[j] = fma(d1, xv[j], acc1[j]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+          for (int o = LC; o < 32; o <<= 1) {
+            acc0[j] += __shfl_xor_sync(0xffffffffu, acc0[j], o);
+            acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], o);
+          }
+        }
+        if (kl == 0 && cok) {
+          if (res_smem) {
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+              sst<W>(res_t + (uint32_t)(((col + j) * kTileRows + ra) * ebw), acc0[j]);
+              sst<W>(res_t + (uint32_t)(((col + j) * kTileRows + rb) * ebw), acc1[j]);
+            }
+          } else {
+            if (ra < t.rows) store_cols<W, CPL>(B + (int64_t)(t.row0 + ra) * ldb + col, acc0);
+            if (rb < t.rows) store_cols<W, CPL>(B + (int64_t)(t.row0 + rb) * ldb + col, acc1);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
   }
 
-  for (int c0 = 0; c0 < R; c0 += CT) {
-    const int nc = min(CT, R - c0);
-    for (int e = threadIdx.x; e < lf.m * CT; e += kThreads) {
-      const int j = e / CT, jj = e - j * CT;
-      Zx[e] = jj < nc ? X[(int64_t)(lf.row0 + j) * ldx + c0 + jj] : (W)0;
+  // ---- every Y_node is in the gathered Y after the second stage ----
+  if (tid == 0 && ntiles) grid_wait(sync, sync_base + 2ull * (unsigned long long)G, hd.err);
+  bar_consumers();   // also: pass-1 results are complete for every warp
+
+  // ---- pass 2: warp (tl mod kCWarps) takes tile tl alone, lane r = row r:
+  //      B[row] = (pass 1) + sum_q U[row, q] Y[q, :].  The ring is idle now;
+  //      each warp copies its tile's header and U rows and the leaf's
+  //      gathered-Y block into its own slice of the ring's memory ----
+  const size_t wslice = ((size_t)nstages * stage_bytes / kCWarps) / 128 * 128;
+  uint8_t* wbuf = stages + (size_t)warp * wslice;
+  for (int tl = warp, use = 0; tl < ntiles && alive; tl += kCWarps, ++use) {
+    const P2Tile* tp = hd.p2 + blockIdx.x + (int64_t)tl * G;
+    const int64_t toff = __ldg(&tp->off);
+    const int nq = __ldg(&tp->nq), hbytes = __ldg(&tp->hbytes), ubytes = __ldg(&tp->ubytes);
+    const int nlev = hd.depth;   // header entries
+    const int rows = __ldg(&tp->rows), row0 = __ldg(&tp->row0), yrow = __ldg(&tp->yrow);
+    const uint32_t ybytes = (uint32_t)(((int64_t)nq * R * ebw + 15) / 16 * 16);
+    const uint32_t res_t = smem_u32(res) + (uint32_t)((size_t)tl * kTileRows * R * ebw);
+    const int r = lane;
+    const bool staged = (size_t)(hbytes + ubytes) + ybytes <= wslice;
+    uint32_t hdr_a, ys_a;
+    const uint8_t* hdr_g = hd.pool + toff;
+    if (staged) {
+      hdr_a = smem_u32(wbuf);
+      ys_a = hdr_a + (uint32_t)(hbytes + ubytes);
+      uint64_t* bar = &wbarA[warp];
+      if (lane == 0) {
+        // earlier generic reads of this memory (pass 1) before the async copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, (uint32_t)(hbytes + ubytes) + ybytes);
+        if (hbytes + ubytes) bulk_g2s(wbuf, hdr_g, (uint32_t)(hbytes + ubytes), bar);
+        if (ybytes) bulk_g2s(wbuf + hbytes + ubytes, Yg + (int64_t)yrow * R, ybytes, bar);
+      }
+      __syncwarp();
+      if (!mbar_wait(bar, use & 1, hd.err, 7)) {
+        alive = false;
+        break;
+      }
     }
-    __syncthreads();
-
-    W acc[4][CT];
+    for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
+      const int nc = min(kMaxColsLane, R - c0);
+      W acc[kMaxColsLane];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int j = 0; j < CT; ++j) acc[q][j] = (W)0;
-
-    // leaf block: does not depend on phase 1
-    if (active) {
-      const uint8_t* db = hd.pool + lf.offD + (int64_t)rowbase * ebw;
-      const int64_t colstride = (int64_t)lf.pm * ebw;
-      constexpr int kBatch = 8;
-      for (int j0 = g; j0 < lf.m; j0 += kBatch * kP2Groups) {
-        Vec4<W> d[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int j = j0 + u * kP2Groups;
-          if (j < lf.m) d[u] = load4<W>(db + (int64_t)j * colstride, wprec);
+      for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+      // level by level (the format is fixed within a level): one dispatch on
+      // the format per level, then a loop over the level's U columns
+      int q = 0;
+      for (int lv = 0; lv < nlev; ++lv) {
+        uint32_t w0, w1;
+        if (staged) {
+          w0 = sld_u32(hdr_a + 8u * lv);
+          w1 = sld_u32(hdr_a + 8u * lv + 4u);
+        } else {
+          const uint2 w = __ldg(reinterpret_cast<const uint2*>(hdr_g) + lv);
+          w0 = w.x;
+          w1 = w.y;
         }
+        const int rU = (int)(w1 & 0xffffu), tier = (int)(w1 >> 16);
+        auto level = [&](auto tc) {
+          constexpr int TIER = decltype(tc)::value;
+          constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+          if (staged) {
+            const uint32_t ucol = hdr_a + (uint32_t)hbytes + w0 + (uint32_t)(r * eb);
+#pragma unroll 2
+            for (int c = 0; c < rU; ++c) {
+              const W u = sld_fmt<W, TIER>(ucol + (uint32_t)(c * kTileRows * eb));
+              const uint32_t yq = ys_a + (uint32_t)(((q + c) * R + c0) * ebw);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          const int j = j0 + u * kP2Groups;
-          if (j < lf.m) {
-            const W* z = Zx + j * CT;
-#pragma unroll
-            for (int jj = 0; jj < CT; ++jj) {
-              const W zz = z[jj];
-              acc[0][jj] = fma(d[u].x, zz, acc[0][jj]);
-              acc[1][jj] = fma(d[u].y, zz, acc[1][jj]);
-              acc[2][jj] = fma(d[u].z, zz, acc[2][jj]);
-              acc[3][jj] = fma(d[u].w, zz, acc[3][jj]);
+              for (int j = 0; j < kMaxColsLane; ++j)
+                if (j < nc) acc[j] = fma(u, sld<W>(yq + (uint32_t)(j * ebw)), acc[j]);
             }
+          } else {
+            // too large for the slice: U and Y read directly
+            const uint8_t* ucol = hdr_g + hbytes + w0 + r * eb;
+            const W* yb = Yg + (int64_t)(yrow + q) * R + c0;
+#pragma unroll 2
+            for (int c = 0; c < rU; ++c) {
+              const W u = gld_fmt<W, TIER>(ucol + (int64_t)c * kTileRows * eb);
+#pragma unroll
+              for (int j = 0; j < kMaxColsLane; ++j)
+                if (j < nc) acc[j] = fma(u, __ldcg(yb + (int64_t)c * R + j), acc[j]);
+            }
+          }
+        };
+        switch (tier) {
+          case HODLR_FP64: level(std::integral_constant<int, HODLR_FP64>{}); break;
+          case HODLR_FP32: level(std::integral_constant<int, HODLR_FP32>{}); break;
+          case HODLR_FP16: level(std::integral_constant<int, HODLR_FP16>{}); break;
+          case HODLR_BF16: level(std::integral_constant<int, HODLR_BF16>{}); break;
+          case HODLR_E4M3: level(std::integral_constant<int, HODLR_E4M3>{}); break;
+          default: level(std::integral_constant<int, HODLR_E5M2>{}); break;
+        }
+        q += rU;
+      }
+      if (r < rows) {
+        W* brow = B + (int64_t)(row0 + r) * ldb + c0;
+#pragma unroll
+        for (int j = 0; j < kMaxColsLane; ++j) {
+          if (j < nc) {
+            const W p = res_smem ? sld<W>(res_t + (uint32_t)(((c0 + j) * kTileRows + r) * ebw)) : brow[j];
+            brow[j] = p + acc[j];
           }
         }
       }
     }
-
-    // Y comes from phase 1
-    pdl_wait();
-    for (int k = 1; k <= depth; ++k) {
-      const int a = s_anc[k];
-      const int ia = it.leaf >> (depth - k);
-      const int sib = node_index(k, ia ^ 1);
-      const NodeDev na = hd.nodes[a];
-      const int yo = hd.nodes[sib].yoff;
-      const W invs = (W)na.invsU;
-      for (int e = threadIdx.x; e < na.rU * CT; e += kThreads) {
-        const int c = e / CT, jj = e - c * CT;
-        Zy[(s_q0[k] + c) * CT + jj] = jj < nc ? Y[(int64_t)(yo + c) * R + c0 + jj] * invs : (W)0;
-      }
-    }
-    __syncthreads();
-
-    if (active) {
-      for (int q = g; q < totq; q += kP2Groups) {
-        const int p = qprec[q];
-        const Vec4<W> u = load4<W>(hd.pool + qoff[q] + (int64_t)4 * l * prec_bytes(p), p);
-        const W* z = Zy + q * CT;
-#pragma unroll
-        for (int jj = 0; jj < CT; ++jj) {
-          const W zz = z[jj];
-          acc[0][jj] = fma(u.x, zz, acc[0][jj]);
-          acc[1][jj] = fma(u.y, zz, acc[1][jj]);
-          acc[2][jj] = fma(u.z, zz, acc[2][jj]);
-          acc[3][jj] = fma(u.w, zz, acc[3][jj]);
-        }
-      }
-    }
-    // the 4 groups of a warp (lane bits 3 and 4) first, then the warps in order
-    const int warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int jj = 0; jj < CT; ++jj) {
-        W v = acc[q][jj];
-        v += __shfl_xor_sync(0xffffffffu, v, 8);
-        v += __shfl_xor_sync(0xffffffffu, v, 16);
-        if ((threadIdx.x & 31) < kP2Lanes) red[((size_t)warp * kP2Rows + 4 * l + q) * CT + jj] = v;
-      }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kP2Rows * CT; e += kThreads) {
-      const int row = e / CT, jj = e - row * CT;
-      W s = (W)0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += red[(size_t)w * kP2Rows * CT + e];
-      if (it.t0 + row < lf.m && jj < nc) B[(int64_t)(lf.row0 + it.t0 + row) * ldb + c0 + jj] = s;
-    }
-    __syncthreads();
+    __syncwarp();   // every lane is done with the slice before the next copy
   }
 }
 
-template <typename W, int CT>
-cudaError_t launch_ct(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb,
-                      W* Y, W* partials, unsigned* counters, cudaStream_t s, cudaEvent_t* ev) {
-  if (ev) cudaEventRecord(ev[0], s);
-  if (hd.n_p1 > 0) {
-    phase1_kernel<W, CT><<<hd.n_p1, kThreads, 0, s>>>(hd, X, ldx, nrhs, Y, partials, counters);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+constexpr int kXStageMax = 32 * 1024;   // stage X through shared memory up to this size
+constexpr int kResMax = 32 * 1024;      // pass-1 results in shared memory up to this size
+
+// shared memory besides the stages and the pass-1 results: barriers and
+// descriptors
+size_t kernel_fixed_smem() {
+  return (size_t)(2 * kMaxStages + kCWarps) * sizeof(uint64_t) + (size_t)kMaxStages * sizeof(P2Tile) + 128;
+}
+
+int n_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   }
-  if (ev) cudaEventRecord(ev[1], s);
-  const size_t smem = phase2_smem_bytes<W, CT>(hd);
-  static size_t smem_set = 48 * 1024;   // per instantiation: largest size opted in so far
+  return n;
+}
+
+int smem_optin() {
+  static int v = 0;
+  if (!v) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  return v;
+}
+
+template <typename W, int LC, int CPL>
+cudaError_t launch_lc(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb, W* Y,
+                      W* partials, unsigned long long* sync, unsigned long long sync_base, cudaStream_t s,
+                      cudaEvent_t* ev) {
+  // X rows go through shared memory (a bulk copy with each tile) when they
+  // are contiguous, 16-byte aligned and small enough
+  const int64_t xb = (int64_t)hd.leaf_m_max * nrhs * (int)sizeof(W);
+  const bool x_tma = hd.x_aligned && ldx == nrhs && ((uintptr_t)X % 16) == 0 && xb <= kXStageMax;
+  const int xstage = x_tma ? (int)((xb + 127) / 128 * 128) : 0;
+  // pass-1 results of this CTA's tiles in shared memory when small enough
+  const int G = n_sms();
+  const int64_t tiles_cta = (hd.n_p2 + G - 1) / G;
+  const int64_t rb = (tiles_cta * kTileRows * nrhs * (int64_t)sizeof(W) + 127) / 128 * 128;
+  const int res_smem = rb <= kResMax ? 1 : 0;
+  const size_t fixed = kernel_fixed_smem() + (res_smem ? rb : 0);
+  const size_t per_stage = (size_t)hd.stage_bytes + xstage;
+  const int nstages = (int)std::min<size_t>(kMaxStages, ((size_t)smem_optin() - fixed) / per_stage);
+  if (nstages < 1) return cudaErrorInvalidConfiguration;   // the host sizes batches so this cannot happen
+  const size_t smem = fixed + per_stage * nstages;
+  static size_t smem_set = 0;   // per instantiation: largest size opted in so far
   if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(phase2_kernel<W, CT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(matvec_kernel<W, LC, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(hd.n_p2);
-  cfg.blockDim = dim3(kThreads);
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kP2Threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = (hd.n_p1 > 0 && !ev) ? 1 : 0;
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, phase2_kernel<W, CT>, hd, X, ldx, nrhs, (const W*)Y, B, ldb);
+  if (ev) cudaEventRecord(ev[0], s);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, matvec_kernel<W, LC, CPL>, hd, X, ldx, nrhs, Y, partials, B, ldb,
+                                     sync, sync_base, nstages, xstage, res_smem);
   if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+  }
   return cudaGetLastError();
 }
 
+// Lane layout for nrhs columns: LC = the smallest power of two >= nrhs (at
+// most 32); two columns per lane for nrhs > 32 in fp32 when every row of X, B
+// and the scratch starts on an 8-byte boundary.
 template <typename W>
-cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb,
-                     W* Y, W* partials, unsigned* counters, cudaStream_t s, cudaEvent_t* ev) {
-  if (nrhs == 1) return launch_ct<W, 1>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
-  if (nrhs == 2) return launch_ct<W, 2>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
-  if (nrhs <= 4) return launch_ct<W, 4>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
-  return launch_ct<W, 8>(hd, nrhs, X, ldx, B, ldb, Y, partials, counters, s, ev);
+cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb, W* Y,
+                     W* partials, unsigned long long* sync, unsigned long long base, cudaStream_t s,
+                     cudaEvent_t* ev) {
+#define HODLR_LAUNCH(LC, CPL) launch_lc<W, LC, CPL>(hd, nrhs, X, ldx, B, ldb, Y, partials, sync, base, s, ev)
+  if (nrhs == 1) return HODLR_LAUNCH(1, 1);
+  if (nrhs == 2) return HODLR_LAUNCH(2, 1);
+  if (nrhs <= 4) return HODLR_LAUNCH(4, 1);
+  if (nrhs <= 8) return HODLR_LAUNCH(8, 1);
+  if (nrhs <= 16) return HODLR_LAUNCH(16, 1);
+  if constexpr (sizeof(W) == 4) {
+    const bool pairs = nrhs > 32 && nrhs % 2 == 0 && ldx % 2 == 0 && ldb % 2 == 0 &&
+                       (uintptr_t)X % 8 == 0 && (uintptr_t)B % 8 == 0;
+    if (pairs) return HODLR_LAUNCH(32, 2);
+  }
+  return HODLR_LAUNCH(32, 1);
+#undef HODLR_LAUNCH
 }
 
 }  // namespace
 
+int matvec_grid(const HandleDev& hd) {
+  (void)hd;
+  return n_sms();
+}
+
+unsigned long long matvec_sync_step(const HandleDev& hd) {
+  return 2ull * (unsigned long long)matvec_grid(hd);   // two arrivals per CTA
+}
+
+// Up to kMaxCols columns per launch: X rows of a chunk or a tile then fit
+// one shared-memory stage (512 or leaf rows x 16 x 4 bytes <= 32 KiB);
+// wider products run in batches of columns.
+constexpr int kMaxCols = 16;
+
+int matvec_max_batch(const HandleDev& hd, int work) {
+  const int ebw = prec_bytes(work);
+  const size_t fixed = kernel_fixed_smem();
+  const int64_t room = (int64_t)smem_optin() - (int64_t)fixed - hd.stage_bytes - 256;
+  if (room <= 0) return 0;
+  (void)ebw;
+  return kMaxCols;
+}
+
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
-                          void* B, int64_t ldb, void* Y, void* partials, unsigned* counters,
+                          void* B, int64_t ldb, void* Y, void* partials,
+                          unsigned long long* sync, unsigned long long sync_base,
                           cudaStream_t s, cudaEvent_t* ev) {
   if (work == HODLR_FP64)
-    return launch_w<double>(hd, nrhs, (const double*)X, ldx, (double*)B, ldb, (double*)Y,
-                            (double*)partials, counters, s, ev);
-  return launch_w<float>(hd, nrhs, (const float*)X, ldx, (float*)B, ldb, (float*)Y,
-                         (float*)partials, counters, s, ev);
+    return launch_w<double>(hd, nrhs, (const double*)X, ldx, (double*)B, ldb, (double*)Y, (double*)partials,
+                            sync, sync_base, s, ev);
+  return launch_w<float>(hd, nrhs, (const float*)X, ldx, (float*)B, ldb, (float*)Y, (float*)partials, sync,
+                         sync_base, s, ev);
 }
 
 }  // namespace hodlr

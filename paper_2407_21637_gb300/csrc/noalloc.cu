@@ -1,7 +1,7 @@
 // hodlr_matvec_noalloc: the HODLR product without any device allocation.
 //
-// hodlr_matvec keeps its scratch (the phase-1 partial sums, the V^T X
-// results and the per-node completion counters) in buffers the handle
+// hodlr_matvec keeps its scratch (the partial sums of V^T X, the gathered
+// V^T X results and a grid barrier counter) in buffers the handle
 // allocated when it was created.  This variant keeps that scratch in one
 // file-scope device array instead, so a call never reaches cudaMalloc, and
 // it does not touch the handle's own scratch.  It is meant for callers that
@@ -68,31 +68,36 @@ extern "C" hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void
   const size_t span_b = ((size_t)(h->n - 1) * ldb + nrhs) * es;
   if (!(xb + span_x <= bb || bb + span_b <= xb)) return set_error(HODLR_EINVAL, "X and B overlap");
 
-  // scratch layout: counters (one per node), then Y and the partial sums for
-  // one batch of nb right-hand sides
-  const size_t counter_bytes = ((sizeof(unsigned) * std::max(h->hd.n_nodes, 1)) + 255) / 256 * 256;
+  // scratch layout: the grid counter (kSyncHeadBytes), then, per batch of
+  // nb columns, the gathered Y (y_rows * nb values + 4 of slack, rounded to
+  // 256 bytes) and the partial sums (p_rows * nb values)
+  const size_t counter_bytes = kSyncHeadBytes;
   const size_t per_col = ((size_t)h->hd.y_rows + (size_t)h->hd.p_rows) * es;
-  if (counter_bytes + per_col > kNoAllocScratchBytes)
+  const size_t fixed = counter_bytes + 4 * es + 512;
+  if (fixed + per_col > kNoAllocScratchBytes)
     return set_error(HODLR_EINVAL, "matrix too large for the 4 MiB static scratch of hodlr_matvec_noalloc "
                                    "(use hodlr_matvec)");
-  const int nb_max = (int)std::min<size_t>((size_t)nrhs, per_col ? (kNoAllocScratchBytes - counter_bytes) / per_col
-                                                                 : (size_t)nrhs);
+  const int nb_max = (int)std::min<size_t>(std::min<size_t>((size_t)nrhs, (size_t)h->batch),
+                                           (kNoAllocScratchBytes - fixed) / per_col);
   void* base = nullptr;
   hodlr_status st = scratch_for_current_device(&base);
   if (st != HODLR_OK) return st;
-  unsigned* counters = (unsigned*)base;
+  unsigned long long* sync = (unsigned long long*)base;
   char* ybuf = (char*)base + counter_bytes;
   cudaStream_t s = (cudaStream_t)stream;
-  // The array keeps the previous call's contents: the counters must start at zero.
-  cudaError_t e = cudaMemsetAsync(counters, 0, counter_bytes, s);
-  if (e != cudaSuccess) return set_cuda_error(e, "cudaMemsetAsync(counters)");
+  // The array keeps the previous call's contents: the counter must start at
+  // zero.
+  cudaError_t e = cudaMemsetAsync(sync, 0, counter_bytes, s);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaMemsetAsync(grid counter)");
+  unsigned long long base_count = 0;
   for (int c0 = 0; c0 < nrhs; c0 += nb_max) {
     const int nb = std::min(nb_max, nrhs - c0);
     void* Y = ybuf;
-    void* partials = ybuf + (size_t)h->hd.y_rows * nb * es;
-    e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, Y, partials, counters, s,
-                      nullptr);
+    void* partials = ybuf + (((size_t)h->hd.y_rows * nb + 4) * es + 255) / 256 * 256;
+    e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, Y, partials, sync, base_count,
+                      s, nullptr);
     if (e != cudaSuccess) return set_cuda_error(e, "hodlr_matvec_noalloc launch");
+    base_count += matvec_sync_step(h->hd);
   }
   return HODLR_OK;
 }
