@@ -377,6 +377,23 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       pool += region;
     }
   }
+  // tensor-core groups: up to four consecutive tiles (128 rows) of a leaf
+  std::vector<TcGroup> tcg;
+  for (size_t t = 0; t < h->p2.size();) {
+    const P2Tile& t0 = h->p2[t];
+    TcGroup gr;
+    memset(&gr, 0, sizeof(gr));
+    gr.row0 = t0.row0;
+    gr.xrow0 = t0.xrow0;
+    gr.m = t0.m;
+    while (t < h->p2.size() && gr.ntl < 4 && h->p2[t].xrow0 == t0.xrow0) {
+      const P2Tile& tt = h->p2[t];
+      gr.doff[gr.ntl++] = tt.off + tt.hbytes + tt.ubytes;
+      gr.rows += tt.rows;
+      ++t;
+    }
+    tcg.push_back(gr);
+  }
   pool = align_up(std::max<size_t>(pool, 256), 256);
   h->pool_bytes = pool;
   if (cudaMalloc((void**)&h->d_pool, pool) != cudaSuccess) return fail(HODLR_ENOMEM, "factor pool");
@@ -499,6 +516,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     return h->nred[x.x].nparts > h->nred[y.x].nparts;
   });
   if ((st = upload(ritems, &h->d_ritems)) != HODLR_OK) return st;
+  if ((st = upload(tcg, &h->d_tcg)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
   if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
   // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
@@ -528,6 +546,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   hd.yscat = h->d_yscat;
   hd.ritems = h->d_ritems;
   hd.n_ritems = (int)ritems.size();
+  hd.tcg = h->d_tcg;
+  hd.n_tcg = (int)tcg.size();
   hd.pool = h->d_pool;
   hd.err = h->d_err;
   hd.n = n;
@@ -554,7 +574,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   h->batch = std::min(h->max_nrhs, mb);
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
                                h->leaves.size() * sizeof(LeafDev) + h->vch.size() * sizeof(VChunk) +
-                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
+                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
   return HODLR_OK;
 }
 
@@ -670,12 +690,34 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   const size_t span_x = ((size_t)(h->n - 1) * ldx + nrhs) * es, span_b = ((size_t)(h->n - 1) * ldb + nrhs) * es;
   if (!(xb + span_x <= bb || bb + span_b <= xb)) return fail(HODLR_EINVAL, "X and B overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int c0 = 0; c0 < nrhs; c0 += h->batch) {
-    const int nb = std::min(h->batch, nrhs - c0);
-    const bool last = c0 + h->batch >= nrhs;
-    cudaError_t e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y,
-                                  h->d_partials, h->d_sync, h->sync_base, s,
-                                  (h->prof_on && last) ? h->prof_ev : nullptr);
+  // fp32 work with many right-hand sides: leaf products on the tensor cores
+  // (batches of up to kTcMaxCols columns), low-rank part in the product
+  // kernel; otherwise the product kernel alone (batches of h->batch)
+  const bool tc = h->work == HODLR_FP32 && nrhs >= kTcMinCols && h->hd.n_tcg > 0;
+  const int step = tc ? std::min(h->max_nrhs, kTcMaxCols) : h->batch;
+  for (int c0 = 0; c0 < nrhs; c0 += step) {
+    const int nb = std::min(step, nrhs - c0);
+    const bool last = c0 + step >= nrhs;
+    cudaEvent_t* ev = (h->prof_on && last) ? h->prof_ev : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (tc && nb >= kTcMinCols) {
+      if (ev) cudaEventRecord(ev[0], s);
+      e = launch_leaf_tc(h->hd.tcg, h->hd.n_tcg, h->hd.pool, (const float*)(xb + c0 * es), ldx, nb,
+                         (float*)(bb + c0 * es), ldb, h->d_err, s);
+      if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec leaf launch");
+      if (ev) cudaEventRecord(ev[1], s);
+      e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y, h->d_partials,
+                        h->d_sync, h->sync_base, s, nullptr, 1);
+      if (ev) cudaEventRecord(ev[2], s);
+    } else {
+      for (int d0 = 0; d0 < nb && e == cudaSuccess; d0 += h->batch) {
+        const int nd = std::min(h->batch, nb - d0);
+        const bool lastd = d0 + h->batch >= nb;
+        e = launch_matvec(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_Y,
+                          h->d_partials, h->d_sync, h->sync_base, s, lastd ? ev : nullptr);
+        if (!lastd) h->sync_base += matvec_sync_step(h->hd);
+      }
+    }
     h->sync_base += matvec_sync_step(h->hd);
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
   }

@@ -14,6 +14,7 @@ using hodlr::VChunk;
 using hodlr::NodeRed;
 using hodlr::P1Seg;
 using hodlr::P2Tile;
+using hodlr::TcGroup;
 using hodlr::PackTask;
 using hodlr::HandleDev;
 
@@ -42,6 +43,7 @@ struct hodlr_s {
   VChunk* d_vch = nullptr;
   NodeRed* d_nred = nullptr;
   int2* d_ritems = nullptr;
+  TcGroup* d_tcg = nullptr;
   P2Tile* d_p2 = nullptr;
   int32_t* d_yscat = nullptr;
   int* d_err = nullptr;
@@ -63,6 +65,7 @@ struct hodlr_s {
     cudaFree(d_vch);
     cudaFree(d_nred);
     cudaFree(d_ritems);
+    cudaFree(d_tcg);
     cudaFree(d_p2);
     cudaFree(d_yscat);
     cudaFree(d_err);

@@ -105,6 +105,20 @@ struct P2Tile {
   int32_t ubytes;                 // U bytes (multiple of 16); D starts at hbytes + ubytes
 };
 
+// Tensor-core leaf products (fp32 work, many right-hand sides): a group is
+// up to 128 consecutive rows of one leaf, i.e. up to four product tiles.
+constexpr int kTcMinCols = 16;    // products with at least this many columns use them
+constexpr int kTcMaxCols = 64;    // columns per launch at most (MMA N)
+struct TcGroup {
+  int64_t doff[4];                // byte offset of each tile's leaf-block part in the pool
+  int32_t ntl;                    // tiles in the group (1..4)
+  int32_t rows;                   // valid rows (<= 128)
+  int32_t row0;                   // first row of the group
+  int32_t xrow0;                  // first row of the leaf (row of X for column 0)
+  int32_t m;                      // leaf rows = D columns
+  int32_t pad_;
+};
+
 // Device-resident description of a handle (passed by value to kernels).
 // The gathered Y: for every leaf, the rows Y_{a_k ^ 1} (k = 1..depth) its
 // tiles need, in the order of the tile's U columns, one block per leaf
@@ -119,10 +133,11 @@ struct HandleDev {
   const P2Tile* p2;
   const int32_t* yscat;
   const int2* ritems;             // reduction items: (NodeRed index, row of Y_node), all nodes
+  const TcGroup* tcg;             // tensor-core leaf groups
   const uint8_t* pool;
   int* err;                       // device error word (bounded waits that gave up)
   int32_t n, depth, n_nodes, n_leaves;
-  int32_t n_vch, n_nred, n_p2, n_ritems;
+  int32_t n_vch, n_nred, n_p2, n_ritems, n_tcg;
   int32_t chunk_xrows_max;        // largest real-row span of a V chunk
   int32_t y_rows, p_rows;         // rows of the gathered Y and of the partial buffer
   int32_t max_nq;                 // largest U column count of a tile
@@ -305,7 +320,11 @@ cudaError_t launch_unpack(const uint8_t* pool, const PackTask* tasks, int ntasks
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, void* Y, void* partials,
                           unsigned long long* sync, unsigned long long sync_base,
-                          cudaStream_t s, cudaEvent_t* ev);
+                          cudaStream_t s, cudaEvent_t* ev, int skip_leaf = 0);
+// Leaf products on the tensor cores (fp32 work, kTcMinCols <= nrhs <=
+// kTcMaxCols): B[rows of every leaf] = D_i X[I_i].
+cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const uint8_t* pool, const float* X, int64_t ldx,
+                           int nrhs, float* B, int64_t ldb, int* err, cudaStream_t s);
 // The grid size launch_matvec uses.
 int matvec_grid(const HandleDev& hd);
 // How far one launch advances the grid barrier counter (sync_base of the

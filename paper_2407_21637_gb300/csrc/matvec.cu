@@ -98,7 +98,7 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
 // completes within microseconds), then sleeps in try_wait; false (and the
 // error word set) if the phase has not completed within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
-  for (int k = 0; k < 4096; ++k)
+  for (int k = 0; k < 4; ++k)
     if (mbar_test_wait(bar, parity)) return true;
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
@@ -258,6 +258,18 @@ __device__ __forceinline__ W sld_fmt(uint32_t a) {
   }
 }
 
+// Calls f with the storage format as a compile-time constant (an if-chain,
+// fp32 first).
+template <typename F>
+__device__ __forceinline__ void with_format(int tier, F&& f) {
+  if (tier == HODLR_FP32) f(std::integral_constant<int, HODLR_FP32>{});
+  else if (tier == HODLR_BF16) f(std::integral_constant<int, HODLR_BF16>{});
+  else if (tier == HODLR_FP16) f(std::integral_constant<int, HODLR_FP16>{});
+  else if (tier == HODLR_FP64) f(std::integral_constant<int, HODLR_FP64>{});
+  else if (tier == HODLR_E4M3) f(std::integral_constant<int, HODLR_E4M3>{});
+  else f(std::integral_constant<int, HODLR_E5M2>{});
+}
+
 __device__ __forceinline__ void bar_consumers() {
   asm volatile("bar.sync 1, %0;" ::"r"(kCThreads) : "memory");
 }
@@ -298,7 +310,7 @@ template <typename W, int LC, int CPL>
 __global__ void __launch_bounds__(kP2Threads, 1)
 matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W* __restrict__ Yg,
               W* __restrict__ partials, W* __restrict__ B, int64_t ldb, unsigned long long* sync,
-              unsigned long long sync_base, int nstages, int xstage_bytes, int res_smem) {
+              unsigned long long sync_base, int nstages, int xstage_bytes, int res_smem, int skip_leaf) {
   using L = Lanes<LC, CPL>;
   constexpr int LK = L::LK, BW = L::BW, RTA = L::RTA;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -376,7 +388,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 
   if (warp == kCWarps) {
     // ================= producer: the leaf blocks of this CTA's tiles =================
-    if (lane != 0) return;
+    if (lane != 0 || skip_leaf) return;
     int i = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < hd.n_p2; tile += G, ++i) {
@@ -443,14 +455,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             }
           }
         };
-        switch (tier) {
-          case HODLR_FP64: run(std::integral_constant<int, HODLR_FP64>{}); break;
-          case HODLR_FP32: run(std::integral_constant<int, HODLR_FP32>{}); break;
-          case HODLR_FP16: run(std::integral_constant<int, HODLR_FP16>{}); break;
-          case HODLR_BF16: run(std::integral_constant<int, HODLR_BF16>{}); break;
-          case HODLR_E4M3: run(std::integral_constant<int, HODLR_E4M3>{}); break;
-          default: run(std::integral_constant<int, HODLR_E5M2>{}); break;
-        }
+        with_format(tier, run);
         // lanes of one column: fixed butterfly; the chunk's partial
 #pragma unroll
         for (int a = 0; a < RTA; ++a)
@@ -477,7 +482,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   static_assert(kTileRows == 32, "one lane per tile row in pass 2");
   {
     const int ra = 2 * warp, rb = 2 * warp + 1;
-    for (int tl = 0; tl < ntiles; ++tl) {
+    for (int tl = 0; tl < (skip_leaf ? 0 : ntiles); ++tl) {
       const int s = tl % nstages;
       if (!mbar_wait(&full[s], (tl / nstages) & 1, hd.err, 4)) {
         alive = false;
@@ -578,8 +583,9 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 
   // ---- pass 2: warp (tl mod kCWarps) takes tile tl alone, lane r = row r:
   //      B[row] = (pass 1) + sum_q U[row, q] Y[q, :].  The ring is idle now;
-  //      each warp copies its tile's header and U rows and the leaf's
-  //      gathered-Y block into its own slice of the ring's memory ----
+  //      each warp copies its tile's header and U rows into its own slice of
+  //      the ring's memory and, for every block of up to 16 columns, loads the
+  //      block of the leaf's gathered Y beside them ----
   const size_t wslice = ((size_t)nstages * stage_bytes / kCWarps) / 128 * 128;
   uint8_t* wbuf = stages + (size_t)warp * wslice;
   for (int tl = warp, use = 0; tl < ntiles && alive; tl += kCWarps, ++use) {
@@ -588,10 +594,9 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     const int nq = __ldg(&tp->nq), hbytes = __ldg(&tp->hbytes), ubytes = __ldg(&tp->ubytes);
     const int nlev = hd.depth;   // header entries
     const int rows = __ldg(&tp->rows), row0 = __ldg(&tp->row0), yrow = __ldg(&tp->yrow);
-    const uint32_t ybytes = (uint32_t)(((int64_t)nq * R * ebw + 15) / 16 * 16);
     const uint32_t res_t = smem_u32(res) + (uint32_t)((size_t)tl * kTileRows * R * ebw);
     const int r = lane;
-    const bool staged = (size_t)(hbytes + ubytes) + ybytes <= wslice;
+    const bool staged = (size_t)(hbytes + ubytes) + (size_t)nq * kMaxColsLane * ebw <= wslice;
     uint32_t hdr_a, ys_a;
     const uint8_t* hdr_g = hd.pool + toff;
     if (staged) {
@@ -601,9 +606,8 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
       if (lane == 0) {
         // earlier generic reads of this memory (pass 1) before the async copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, (uint32_t)(hbytes + ubytes) + ybytes);
+        mbar_arrive_expect_tx(bar, (uint32_t)(hbytes + ubytes));
         if (hbytes + ubytes) bulk_g2s(wbuf, hdr_g, (uint32_t)(hbytes + ubytes), bar);
-        if (ybytes) bulk_g2s(wbuf + hbytes + ubytes, Yg + (int64_t)yrow * R, ybytes, bar);
       }
       __syncwarp();
       if (!mbar_wait(bar, use & 1, hd.err, 7)) {
@@ -613,6 +617,17 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     }
     for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
       const int nc = min(kMaxColsLane, R - c0);
+      if (staged) {
+        // Y[:, c0 .. c0 + nc) of the leaf beside header and U, rows of
+        // kMaxColsLane values (coalesced loads, one round trip)
+        __syncwarp();
+        for (int e = lane; e < nq * kMaxColsLane; e += 32) {
+          const int q = e / kMaxColsLane, j = e - q * kMaxColsLane;
+          const W v = j < nc ? __ldcg(Yg + (int64_t)(yrow + q) * R + c0 + j) : (W)0;
+          sst<W>(ys_a + (uint32_t)(e * ebw), v);
+        }
+        __syncwarp();
+      }
       W acc[kMaxColsLane];
 #pragma unroll
       for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
@@ -638,7 +653,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 #pragma unroll 2
             for (int c = 0; c < rU; ++c) {
               const W u = sld_fmt<W, TIER>(ucol + (uint32_t)(c * kTileRows * eb));
-              const uint32_t yq = ys_a + (uint32_t)(((q + c) * R + c0) * ebw);
+              const uint32_t yq = ys_a + (uint32_t)((q + c) * kMaxColsLane * ebw);
 #pragma unroll
               for (int j = 0; j < kMaxColsLane; ++j)
                 if (j < nc) acc[j] = fma(u, sld<W>(yq + (uint32_t)(j * ebw)), acc[j]);
@@ -656,14 +671,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             }
           }
         };
-        switch (tier) {
-          case HODLR_FP64: level(std::integral_constant<int, HODLR_FP64>{}); break;
-          case HODLR_FP32: level(std::integral_constant<int, HODLR_FP32>{}); break;
-          case HODLR_FP16: level(std::integral_constant<int, HODLR_FP16>{}); break;
-          case HODLR_BF16: level(std::integral_constant<int, HODLR_BF16>{}); break;
-          case HODLR_E4M3: level(std::integral_constant<int, HODLR_E4M3>{}); break;
-          default: level(std::integral_constant<int, HODLR_E5M2>{}); break;
-        }
+        with_format(tier, level);
         q += rU;
       }
       if (r < rows) {
@@ -713,17 +721,17 @@ int smem_optin() {
 template <typename W, int LC, int CPL>
 cudaError_t launch_lc(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb, W* Y,
                       W* partials, unsigned long long* sync, unsigned long long sync_base, cudaStream_t s,
-                      cudaEvent_t* ev) {
+                      cudaEvent_t* ev, int skip_leaf) {
   // X rows go through shared memory (a bulk copy with each tile) when they
   // are contiguous, 16-byte aligned and small enough
   const int64_t xb = (int64_t)hd.leaf_m_max * nrhs * (int)sizeof(W);
-  const bool x_tma = hd.x_aligned && ldx == nrhs && ((uintptr_t)X % 16) == 0 && xb <= kXStageMax;
+  const bool x_tma = !skip_leaf && hd.x_aligned && ldx == nrhs && ((uintptr_t)X % 16) == 0 && xb <= kXStageMax;
   const int xstage = x_tma ? (int)((xb + 127) / 128 * 128) : 0;
   // pass-1 results of this CTA's tiles in shared memory when small enough
   const int G = n_sms();
   const int64_t tiles_cta = (hd.n_p2 + G - 1) / G;
   const int64_t rb = (tiles_cta * kTileRows * nrhs * (int64_t)sizeof(W) + 127) / 128 * 128;
-  const int res_smem = rb <= kResMax ? 1 : 0;
+  const int res_smem = (!skip_leaf && rb <= kResMax) ? 1 : 0;
   const size_t fixed = kernel_fixed_smem() + (res_smem ? rb : 0);
   const size_t per_stage = (size_t)hd.stage_bytes + xstage;
   const int nstages = (int)std::min<size_t>(kMaxStages, ((size_t)smem_optin() - fixed) / per_stage);
@@ -748,7 +756,7 @@ cudaError_t launch_lc(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W*
   cfg.numAttrs = 1;
   if (ev) cudaEventRecord(ev[0], s);
   cudaError_t e = cudaLaunchKernelEx(&cfg, matvec_kernel<W, LC, CPL>, hd, X, ldx, nrhs, Y, partials, B, ldb,
-                                     sync, sync_base, nstages, xstage, res_smem);
+                                     sync, sync_base, nstages, xstage, res_smem, skip_leaf);
   if (e != cudaSuccess) return e;
   if (ev) {
     cudaEventRecord(ev[1], s);
@@ -763,8 +771,9 @@ cudaError_t launch_lc(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W*
 template <typename W>
 cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb, W* Y,
                      W* partials, unsigned long long* sync, unsigned long long base, cudaStream_t s,
-                     cudaEvent_t* ev) {
-#define HODLR_LAUNCH(LC, CPL) launch_lc<W, LC, CPL>(hd, nrhs, X, ldx, B, ldb, Y, partials, sync, base, s, ev)
+                     cudaEvent_t* ev, int skip_leaf) {
+#define HODLR_LAUNCH(LC, CPL) \
+  launch_lc<W, LC, CPL>(hd, nrhs, X, ldx, B, ldb, Y, partials, sync, base, s, ev, skip_leaf)
   if (nrhs == 1) return HODLR_LAUNCH(1, 1);
   if (nrhs == 2) return HODLR_LAUNCH(2, 1);
   if (nrhs <= 4) return HODLR_LAUNCH(4, 1);
@@ -807,12 +816,12 @@ int matvec_max_batch(const HandleDev& hd, int work) {
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, void* Y, void* partials,
                           unsigned long long* sync, unsigned long long sync_base,
-                          cudaStream_t s, cudaEvent_t* ev) {
+                          cudaStream_t s, cudaEvent_t* ev, int skip_leaf) {
   if (work == HODLR_FP64)
     return launch_w<double>(hd, nrhs, (const double*)X, ldx, (double*)B, ldb, (double*)Y, (double*)partials,
-                            sync, sync_base, s, ev);
+                            sync, sync_base, s, ev, skip_leaf);
   return launch_w<float>(hd, nrhs, (const float*)X, ldx, (float*)B, ldb, (float*)Y, (float*)partials, sync,
-                         sync_base, s, ev);
+                         sync_base, s, ev, skip_leaf);
 }
 
 }  // namespace hodlr

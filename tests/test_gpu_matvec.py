@@ -60,9 +60,22 @@ def _gpu(h, eps, work, tiers, per_block=False, max_nrhs=64):
                                     per_block=per_block, max_nrhs=max_nrhs)
 
 
+TC_MIN_COLS = 16   # fp32 products with this many columns use the tensor-core leaf kernel
+
+
 def _tol(h, X, ref, work):
+    """Per-entry bound of the GPU product against the exact product of the
+    stored factors: Higham's standard model for the longest accumulation
+    chain N (gamma_N(u) g + 2u g for the format decode and scaling, u |b| for
+    the final rounding), g = |U|(|V|^T |x|) + |D||x|.  With TC_MIN_COLS or more
+    fp32 columns the leaf products run on the tensor cores as three tf32
+    products (hi*hi + hi*lo + lo*hi); each product then carries up to about
+    3 * 2^-22 = 12u relative error and the fp32 accumulation of the tensor
+    core is allowed 2u per addition: (gamma_N(2u) + 12u) g + u |b|."""
     u = F.unit_roundoff(work)
     g = M.abs_product(h, X)
+    if work == "fp32" and X.shape[1] >= TC_MIN_COLS:
+        return (Bd.gamma(M.max_chain(h), 2 * u) + 14 * u) * g + u * np.abs(ref)
     return (Bd.gamma(M.max_chain(h), u) + 2 * u) * g + u * np.abs(ref)
 
 

@@ -50,7 +50,12 @@ def test_noalloc_matches_matvec_twice(lib, work, R):
     X64 = X.cpu().numpy().astype(np.float64)
     u = F.unit_roundoff(work)
     exact = M.hodlr_matvec(h, X64)
-    tol = (Bd.gamma(M.max_chain(h), u) + 2 * u) * M.abs_product(h, X64) + u * np.abs(exact)
+    g_abs = M.abs_product(h, X64)
+    tol = (Bd.gamma(M.max_chain(h), u) + 2 * u) * g_abs + u * np.abs(exact)
+    # the reference product (hodlr_matvec) runs its leaf products on the
+    # tensor cores from 16 fp32 columns on (three tf32 products)
+    tol_ref = tol if (work != "fp32" or R < 16) else \
+        (Bd.gamma(M.max_chain(h), 2 * u) + 14 * u) * g_abs + u * np.abs(exact)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     for _ in range(2):
         B = torch.full((n, R), float("nan"), dtype=X.dtype, device="cuda")
@@ -58,7 +63,7 @@ def test_noalloc_matches_matvec_twice(lib, work, R):
                                       ctypes.c_void_p(B.data_ptr()), R, PREC[work], stream)
         assert st == 0, lib.hodlr_last_error()
         got = B.cpu().numpy().astype(np.float64)
-        assert np.all(np.abs(got - ref) <= 2 * tol)
+        assert np.all(np.abs(got - ref) <= tol + tol_ref)
         assert np.all(np.abs(got - exact) <= tol)
     g.close()
 
