@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kCWarps = kConsumerWarps;       // consumer warps of the product kernel
 constexpr int kCThreads = 32 * kCWarps;
-constexpr int kRedWarps = 4;                  // node-reduction warps
+constexpr int kRedWarps = 3;                  // node-reduction warps
 constexpr int kP2Threads = kCThreads + 32 + 32 * kRedWarps;   // consumers, producer, reducers
 constexpr int kMaxStages = 6;
 constexpr int kMaxColsLane = 16;              // right-hand sides per lane and step of pass 2
@@ -151,7 +151,7 @@ template <int LC, int CPL>
 struct Lanes {
   static constexpr int LK = 32 / LC;            // lanes across the summation index
   static constexpr int BW = LC * CPL;           // columns per pass
-  static constexpr int RTA = BW >= 32 ? 4 : 8;  // V columns per phase-A pass
+  static constexpr int RTA = 8;                 // V columns per phase-A pass
 };
 
 // CPL consecutive values of a row (8- or 16-byte aligned when CPL = 2).
@@ -338,29 +338,61 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   }
   __syncthreads();
 
-  if (warp > kCWarps) {
-    // ================= reducers =================
-    // After every CTA's phase A (first stage of the grid counter), the rows
-    // of every node: Y_node[a, :] = invs * sum of its chunk partials (each
-    // lane sums the partials lane, lane + 32, ... in order, then a fixed
-    // butterfly), written to the node's gathered-Y targets.  Then the
-    // second stage of the grid counter.
-    const int rw = warp - kCWarps - 1;
-    if (hd.n_ritems > 0) {
-      if (lane == 0) grid_wait(sync, sync_base + (unsigned long long)G, hd.err);
-      __syncwarp();
-      for (int it = blockIdx.x * kRedWarps + rw; it < hd.n_ritems; it += G * kRedWarps) {
-        const int2 ri = __ldg(hd.ritems + it);
-        const NodeRed* nrp = hd.nred + ri.x;
-        const int P = __ldg(&nrp->nparts), rV = __ldg(&nrp->rV), poff0 = __ldg(&nrp->poff0);
-        const int y0 = __ldg(&nrp->yscat0), ny = __ldg(&nrp->nyscat);
-        const W invs = (W)__ldg(&nrp->invs);
-        const W* pp = partials + (int64_t)(poff0 + ri.y) * R;
-        for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
-          const int nc = min(kMaxColsLane, R - c0);
-          W acc[kMaxColsLane];
+  // ---- node reductions: Y_node[a, :] = invs * sum of its chunk partials
+  //      (each lane sums the partials lane, lane + 32, ... in order, then a
+  //      fixed butterfly), written to the node's gathered-Y targets.  The
+  //      items are sorted heaviest first and dealt to the CTAs in turn (warp
+  //      w of CTA c starts at item w * grid + c) so that no SM gets several
+  //      heavy ones; a warp takes items first, first + stride, ... ----
+  auto reduce_items = [&](int first, int stride) {
+    for (int it = first; it < hd.n_ritems; it += stride) {
+      const int2 ri = __ldg(hd.ritems + it);
+      const NodeRed* nrp = hd.nred + ri.x;
+      const int P = __ldg(&nrp->nparts), rV = __ldg(&nrp->rV), poff0 = __ldg(&nrp->poff0);
+      const int y0 = __ldg(&nrp->yscat0), ny = __ldg(&nrp->nyscat);
+      const W invs = (W)__ldg(&nrp->invs);
+      const W* pp = partials + (int64_t)(poff0 + ri.y) * R;
+      for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
+        const int nc = min(kMaxColsLane, R - c0);
+        W acc[kMaxColsLane];
 #pragma unroll
-          for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+        for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+        if (sizeof(W) == 4 && nc == kMaxColsLane && R % 4 == 0) {
+          // 16 columns as four 16-byte loads per partial, two partials in flight
+          int q = lane;
+          for (; q + 32 < P; q += 64) {
+            const float4* r0 = reinterpret_cast<const float4*>(pp + (int64_t)q * rV * R + c0);
+            const float4* r1 = reinterpret_cast<const float4*>(pp + (int64_t)(q + 32) * rV * R + c0);
+            float4 v0[kMaxColsLane / 4], v1[kMaxColsLane / 4];
+#pragma unroll
+            for (int j4 = 0; j4 < kMaxColsLane / 4; ++j4) {
+              v0[j4] = __ldcg(r0 + j4);
+              v1[j4] = __ldcg(r1 + j4);
+            }
+#pragma unroll
+            for (int j4 = 0; j4 < kMaxColsLane / 4; ++j4) {
+              acc[4 * j4 + 0] += (W)v0[j4].x;
+              acc[4 * j4 + 1] += (W)v0[j4].y;
+              acc[4 * j4 + 2] += (W)v0[j4].z;
+              acc[4 * j4 + 3] += (W)v0[j4].w;
+              acc[4 * j4 + 0] += (W)v1[j4].x;
+              acc[4 * j4 + 1] += (W)v1[j4].y;
+              acc[4 * j4 + 2] += (W)v1[j4].z;
+              acc[4 * j4 + 3] += (W)v1[j4].w;
+            }
+          }
+          if (q < P) {
+            const float4* r0 = reinterpret_cast<const float4*>(pp + (int64_t)q * rV * R + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < kMaxColsLane / 4; ++j4) {
+              const float4 v = __ldcg(r0 + j4);
+              acc[4 * j4 + 0] += (W)v.x;
+              acc[4 * j4 + 1] += (W)v.y;
+              acc[4 * j4 + 2] += (W)v.z;
+              acc[4 * j4 + 3] += (W)v.w;
+            }
+          }
+        } else {
           for (int q = lane; q < P; q += 32) {
             const W* row = pp + (int64_t)q * rV * R + c0;
             W v[kMaxColsLane];
@@ -369,19 +401,41 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 #pragma unroll
             for (int j = 0; j < kMaxColsLane; ++j) acc[j] += v[j];
           }
+        }
 #pragma unroll
-          for (int j = 0; j < kMaxColsLane; ++j) acc[j] = warp_sum(acc[j]) * invs;
-          for (int t = lane; t < ny; t += 32) {
-            W* dst = Yg + (int64_t)(__ldg(hd.yscat + y0 + t) + ri.y) * R + c0;
+        for (int j = 0; j < kMaxColsLane; ++j) acc[j] = warp_sum(acc[j]) * invs;
+        for (int t = lane; t < ny; t += 32) {
+          W* dst = Yg + (int64_t)(__ldg(hd.yscat + y0 + t) + ri.y) * R + c0;
 #pragma unroll
-            for (int j = 0; j < kMaxColsLane; ++j)
-              if (j < nc) dst[j] = acc[j];
-          }
+          for (int j = 0; j < kMaxColsLane; ++j)
+            if (j < nc) dst[j] = acc[j];
         }
       }
+    }
+  };
+  // warps of the CTA that reduce: the reducers, and in skip_leaf mode (no
+  // leaf pass to overlap) the consumers as well
+  constexpr int kAllRed = kCWarps + kRedWarps;
+  constexpr int kRedBar = 32 * kAllRed;   // threads of barrier 3 (skip_leaf mode)
+
+  if (warp > kCWarps) {
+    // ================= reducers =================
+    // After every CTA's phase A (first stage of the grid counter): node
+    // reductions, then the second stage of the grid counter.
+    const int rw = warp - kCWarps - 1;
+    if (hd.n_ritems > 0) {
+      if (lane == 0) grid_wait(sync, sync_base + (unsigned long long)G, hd.err);
+      __syncwarp();
+      if (skip_leaf)
+        reduce_items((kCWarps + rw) * G + blockIdx.x, G * kAllRed);
+      else
+        reduce_items(rw * G + blockIdx.x, G * kRedWarps);
       __threadfence();
     }
-    asm volatile("bar.sync 2, %0;" ::"r"(32 * kRedWarps) : "memory");
+    if (skip_leaf)
+      asm volatile("bar.sync 3, %0;" ::"r"(kRedBar) : "memory");
+    else
+      asm volatile("bar.sync 2, %0;" ::"r"(32 * kRedWarps) : "memory");
     if (rw == 0 && lane == 0) atomicAdd(sync, 1ull);
     return;
   }
@@ -476,6 +530,16 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   __threadfence();
   bar_consumers();
   if (tid == 0) atomicAdd(sync, 1ull);
+  if (skip_leaf) {
+    // no leaf pass to overlap: help with the node reductions
+    if (hd.n_ritems > 0) {
+      if (tid == 0) grid_wait(sync, sync_base + (unsigned long long)G, hd.err);
+      bar_consumers();
+      reduce_items(warp * G + blockIdx.x, G * kAllRed);
+      __threadfence();
+    }
+    asm volatile("bar.sync 3, %0;" ::"r"(kRedBar) : "memory");
+  }
 
   // ---- pass 1: D[rows, :] X[I_i] for every tile; warp w owns rows 2w, 2w + 1 ----
   static_assert(kTileRows == 2 * kCWarps, "two rows per consumer warp");
