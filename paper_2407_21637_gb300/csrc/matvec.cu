@@ -471,7 +471,9 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 
   // ---- phase A: every warp of the grid takes V chunks alone, reading V and
   //      X directly (a chunk is at most kChunkRows rows of one node) ----
-  for (int c = blockIdx.x * kCWarps + warp; c < hd.n_vch; c += G * kCWarps) {
+  // chunks are dealt to the CTAs in turn (warp w of CTA c starts at chunk
+  // w * grid + c), so the wide top-level chunks spread over all SMs
+  for (int c = warp * G + blockIdx.x; c < hd.n_vch; c += G * kCWarps) {
     const VChunk& ch = hd.vch[c];
     const int rV = __ldg(&ch.rV), poff = __ldg(&ch.poff), nseg = __ldg(&ch.nseg), tier = __ldg(&ch.tier);
     const int colbytes = __ldg(&ch.colbytes);
@@ -692,9 +694,38 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
         }
         __syncwarp();
       }
+      // the pass-1 part of this row (shared memory, or B when it did not
+      // fit there or the leaf products came from the tensor-core kernel),
+      // loaded before the U Y loop so the global loads overlap it
+      W* brow = B + (int64_t)(row0 + r) * ldb + c0;
       W acc[kMaxColsLane];
+      const bool bvec = sizeof(W) == 4 && nc == kMaxColsLane && ldb % 4 == 0 &&
+                        (reinterpret_cast<uintptr_t>(brow) & 15) == 0;
+      if (r < rows) {
+        if (res_smem) {
 #pragma unroll
-      for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+          for (int j = 0; j < kMaxColsLane; ++j)
+            acc[j] = j < nc ? sld<W>(res_t + (uint32_t)(((c0 + j) * kTileRows + r) * ebw)) : (W)0;
+        } else if (bvec) {
+#pragma unroll
+          for (int j4 = 0; j4 < kMaxColsLane / 4; ++j4) {
+            const float4 v = *reinterpret_cast<const float4*>(brow + 4 * j4);
+            acc[4 * j4 + 0] = (W)v.x;
+            acc[4 * j4 + 1] = (W)v.y;
+            acc[4 * j4 + 2] = (W)v.z;
+            acc[4 * j4 + 3] = (W)v.w;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < kMaxColsLane; ++j) acc[j] = j < nc ? brow[j] : (W)0;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kMaxColsLane; ++j) acc[j] = (W)0;
+      }
+      W uy[kMaxColsLane];
+#pragma unroll
+      for (int j = 0; j < kMaxColsLane; ++j) uy[j] = (W)0;
       // level by level (the format is fixed within a level): one dispatch on
       // the format per level, then a loop over the level's U columns
       int q = 0;
@@ -720,7 +751,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
               const uint32_t yq = ys_a + (uint32_t)((q + c) * kMaxColsLane * ebw);
 #pragma unroll
               for (int j = 0; j < kMaxColsLane; ++j)
-                if (j < nc) acc[j] = fma(u, sld<W>(yq + (uint32_t)(j * ebw)), acc[j]);
+                if (j < nc) uy[j] = fma(u, sld<W>(yq + (uint32_t)(j * ebw)), uy[j]);
             }
           } else {
             // too large for the slice: U and Y read directly
@@ -731,7 +762,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
               const W u = gld_fmt<W, TIER>(ucol + (int64_t)c * kTileRows * eb);
 #pragma unroll
               for (int j = 0; j < kMaxColsLane; ++j)
-                if (j < nc) acc[j] = fma(u, __ldcg(yb + (int64_t)c * R + j), acc[j]);
+                if (j < nc) uy[j] = fma(u, __ldcg(yb + (int64_t)c * R + j), uy[j]);
             }
           }
         };
@@ -739,13 +770,16 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
         q += rU;
       }
       if (r < rows) {
-        W* brow = B + (int64_t)(row0 + r) * ldb + c0;
+        if (bvec) {
 #pragma unroll
-        for (int j = 0; j < kMaxColsLane; ++j) {
-          if (j < nc) {
-            const W p = res_smem ? sld<W>(res_t + (uint32_t)(((c0 + j) * kTileRows + r) * ebw)) : brow[j];
-            brow[j] = p + acc[j];
-          }
+          for (int j4 = 0; j4 < kMaxColsLane / 4; ++j4)
+            *reinterpret_cast<float4*>(brow + 4 * j4) =
+                make_float4(acc[4 * j4] + uy[4 * j4], acc[4 * j4 + 1] + uy[4 * j4 + 1],
+                            acc[4 * j4 + 2] + uy[4 * j4 + 2], acc[4 * j4 + 3] + uy[4 * j4 + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kMaxColsLane; ++j)
+            if (j < nc) brow[j] = acc[j] + uy[j];
         }
       }
     }
