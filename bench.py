@@ -50,7 +50,7 @@ SAMPLE_DIV = 16
 
 
 TC_MIN_COLS = 16      # fp32 products with this many columns run their leaf products on the tensor cores
-TC_MAX_COLS = 256     # columns per tensor-core launch at most
+TC_MAX_COLS = 64      # columns per tensor-core launch at most
 SIMT_COLS = 16        # columns per launch of the CUDA-core product kernel at most
 MAX_NRHS = 64         # the handle's max_nrhs in this benchmark
 
@@ -291,8 +291,10 @@ def run_ours(args, rank, world, dist):
     peak, peak_kind = _peaks()
     # Algorithmic bytes per launch.  Below TC_MIN_COLS columns one launch of
     # matvec_kernel does all of Algorithm 3.3; from TC_MIN_COLS fp32 columns
-    # on, leaf_tc_kernel does the leaf products (D, X read, B written) and
-    # matvec_kernel the low-rank part (U, V, scales, X read, B read+written).
+    # on, leaf_tc_kernel does the leaf products and V^T X (D, V, X read, B
+    # written) and matvec_kernel the rest (U, scales, B read+written).  U and
+    # V hold half of the factor bytes each (equal ranks and sizes in the two
+    # off-diagonal blocks of every node pair of this workload).
     kernels = {"matvec_kernel": [0.0, 0.0], "leaf_tc_kernel": [0.0, 0.0]}   # bytes, ms
     per_rhs = {}
     for R in rhs:
@@ -303,8 +305,8 @@ def run_ours(args, rank, world, dist):
         row = {"us": ms * 1e3, "GBps": total_bytes / (ms * 1e-3) / 1e9,
                "frac_hbm": total_bytes / (ms * 1e-3) / 1e9 / peak, "alg_bytes": total_bytes}
         if WL["work"] == "fp32" and R >= TC_MIN_COLS:
-            leaf_b = info["leaf_bytes"] + 2 * n * R * es
-            low_b = info["factor_bytes"] + info["scale_bytes"] + 3 * n * R * es
+            leaf_b = info["leaf_bytes"] + info["factor_bytes"] // 2 + 2 * n * R * es
+            low_b = info["factor_bytes"] - info["factor_bytes"] // 2 + info["scale_bytes"] + 2 * n * R * es
             kernels["leaf_tc_kernel"][0] += leaf_b
             kernels["leaf_tc_kernel"][1] += k0
             kernels["matvec_kernel"][0] += low_b

@@ -2,6 +2,7 @@
 // Algorithm 3.2 (on device-computed norms), layout planning and launches.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <memory>
 #include <cstdio>
 #include <cstring>
@@ -386,6 +387,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     gr.row0 = t0.row0;
     gr.xrow0 = t0.xrow0;
     gr.m = t0.m;
+    gr.vtab = -1;   // a leaf group
     while (t < h->p2.size() && gr.ntl < 4 && h->p2[t].xrow0 == t0.xrow0) {
       const P2Tile& tt = h->p2[t];
       gr.doff[gr.ntl++] = tt.off + tt.hbytes + tt.ubytes;
@@ -502,6 +504,57 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     }
   }
 
+  // Tensor-core V groups (fp32 work): the fp32 chunks that cover one run of
+  // rows (one segment: a leaf or a piece of one), for every level, packed
+  // up to kTcRows columns per group in level order.  The other chunks (and
+  // every chunk in other working precisions) stay on the CUDA cores.
+  const int n_tcg_leaf = (int)tcg.size();
+  std::vector<TcVRow> tcv;
+  h->vch_rest.clear();
+  if (h->work == HODLR_FP32) {
+    std::map<std::pair<int, int>, std::vector<int>> by_rows;   // (first row, rows) -> chunks
+    for (int c = 0; c < (int)h->vch.size(); ++c) {
+      const VChunk& ch = h->vch[c];
+      const bool ok = ch.tier == HODLR_FP32 && ch.nseg == 1 && ch.seg[0].m > 0 && ch.seg[0].prel == 0 &&
+                      ch.rV <= kTcRows && ch.off % 16 == 0 && ch.colbytes % 16 == 0;
+      if (ok)
+        by_rows[{ch.seg[0].row0, ch.seg[0].m}].push_back(c);
+      else
+        h->vch_rest.push_back(ch);
+    }
+    for (const auto& kv : by_rows) {
+      TcGroup gr;
+      bool open = false;
+      for (int c : kv.second) {
+        const VChunk& ch = h->vch[c];
+        if (open && gr.rows + ch.rV > kTcRows) {
+          tcg.push_back(gr);
+          open = false;
+        }
+        if (!open) {
+          memset(&gr, 0, sizeof(gr));
+          gr.vtab = (int)tcv.size();
+          gr.xrow0 = kv.first.first;
+          gr.m = kv.first.second;
+          TcVRow unused;
+          memset(&unused, 0, sizeof(unused));
+          unused.prow = -1;
+          tcv.resize(tcv.size() + kTcRows, unused);
+          open = true;
+        }
+        for (int a = 0; a < ch.rV; ++a) {
+          TcVRow& e = tcv[gr.vtab + gr.rows + a];
+          e.off = ch.off + (int64_t)a * ch.colbytes;
+          e.prow = ch.poff + a;
+        }
+        gr.rows += ch.rV;
+      }
+      if (open) tcg.push_back(gr);
+    }
+  } else {
+    h->vch_rest = h->vch;
+  }
+
   // ---- descriptors and scratch on the device ----
   hodlr_status st;
   if ((st = upload(h->nodes, &h->d_nodes)) != HODLR_OK) return st;
@@ -517,6 +570,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   });
   if ((st = upload(ritems, &h->d_ritems)) != HODLR_OK) return st;
   if ((st = upload(tcg, &h->d_tcg)) != HODLR_OK) return st;
+  if ((st = upload(tcv, &h->d_tcv)) != HODLR_OK) return st;
+  if ((st = upload(h->vch_rest, &h->d_vch_rest)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
   if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
   // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
@@ -548,6 +603,10 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   hd.n_ritems = (int)ritems.size();
   hd.tcg = h->d_tcg;
   hd.n_tcg = (int)tcg.size();
+  hd.n_tcg_leaf = n_tcg_leaf;
+  hd.tcv = h->d_tcv;
+  hd.vch_rest = h->d_vch_rest;
+  hd.n_vch_rest = (int)h->vch_rest.size();
   hd.pool = h->d_pool;
   hd.err = h->d_err;
   hd.n = n;
@@ -574,7 +633,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   h->batch = std::min(h->max_nrhs, mb);
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
                                h->leaves.size() * sizeof(LeafDev) + h->vch.size() * sizeof(VChunk) +
-                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
+                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + tcv.size() * sizeof(TcVRow) + h->vch_rest.size() * sizeof(VChunk) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
   return HODLR_OK;
 }
 
@@ -693,7 +752,7 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   // fp32 work with many right-hand sides: leaf products on the tensor cores
   // (batches of up to kTcMaxCols columns), low-rank part in the product
   // kernel; otherwise the product kernel alone (batches of h->batch)
-  const bool tc = h->work == HODLR_FP32 && nrhs >= kTcMinCols && h->hd.n_tcg > 0;
+  const bool tc = h->work == HODLR_FP32 && nrhs >= kTcMinCols && h->hd.n_tcg_leaf > 0;
   const int step = tc ? std::min(h->max_nrhs, kTcMaxCols) : h->batch;
   for (int c0 = 0; c0 < nrhs; c0 += step) {
     const int nb = std::min(step, nrhs - c0);
@@ -702,8 +761,8 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
     cudaError_t e = cudaSuccess;
     if (tc && nb >= kTcMinCols) {
       if (ev) cudaEventRecord(ev[0], s);
-      e = launch_leaf_tc(h->hd.tcg, h->hd.n_tcg, h->hd.pool, (const float*)(xb + c0 * es), ldx, nb,
-                         (float*)(bb + c0 * es), ldb, h->d_err, s);
+      e = launch_leaf_tc(h->hd.tcg, h->hd.n_tcg, h->hd.tcv, h->hd.pool, (const float*)(xb + c0 * es), ldx, nb,
+                         (float*)(bb + c0 * es), ldb, (float*)h->d_partials, h->d_err, s);
       if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec leaf launch");
       if (ev) cudaEventRecord(ev[1], s);
       e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y, h->d_partials,

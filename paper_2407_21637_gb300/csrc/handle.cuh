@@ -15,6 +15,7 @@ using hodlr::NodeRed;
 using hodlr::P1Seg;
 using hodlr::P2Tile;
 using hodlr::TcGroup;
+using hodlr::TcVRow;
 using hodlr::PackTask;
 using hodlr::HandleDev;
 
@@ -28,6 +29,7 @@ struct hodlr_s {
   std::vector<NodeDev> nodes;
   std::vector<LeafDev> leaves;
   std::vector<VChunk> vch;
+  std::vector<VChunk> vch_rest;          // chunks no tensor-core V group covers
   std::vector<NodeRed> nred;
   std::vector<P2Tile> p2;
   std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
@@ -44,6 +46,8 @@ struct hodlr_s {
   NodeRed* d_nred = nullptr;
   int2* d_ritems = nullptr;
   TcGroup* d_tcg = nullptr;
+  TcVRow* d_tcv = nullptr;
+  VChunk* d_vch_rest = nullptr;
   P2Tile* d_p2 = nullptr;
   int32_t* d_yscat = nullptr;
   int* d_err = nullptr;
@@ -66,6 +70,8 @@ struct hodlr_s {
     cudaFree(d_nred);
     cudaFree(d_ritems);
     cudaFree(d_tcg);
+    cudaFree(d_tcv);
+    cudaFree(d_vch_rest);
     cudaFree(d_p2);
     cudaFree(d_yscat);
     cudaFree(d_err);

@@ -105,17 +105,29 @@ struct P2Tile {
   int32_t ubytes;                 // U bytes (multiple of 16); D starts at hbytes + ubytes
 };
 
-// Tensor-core leaf products (fp32 work, many right-hand sides): a group is
-// up to 128 consecutive rows of one leaf, i.e. up to four product tiles.
+// Tensor-core products (fp32 work, many right-hand sides).  A leaf group is
+// up to 128 consecutive rows of one leaf, i.e. up to four product tiles:
+// C = D[rows, :] X[I_i], written to B.  A V group is up to 128 columns of
+// fp32 generators V_j restricted to the same rows I (one V chunk of one
+// leaf, for several levels): C = V_j[I, :]^T X[I], written to the chunks'
+// partial rows; its rows come from the TC row table.
 constexpr int kTcMinCols = 16;    // products with at least this many columns use them
 constexpr int kTcMaxCols = 64;    // columns per launch at most (MMA N)
+constexpr int kTcRows = 128;      // rows per group (MMA M)
 struct TcGroup {
-  int64_t doff[4];                // byte offset of each tile's leaf-block part in the pool
-  int32_t ntl;                    // tiles in the group (1..4)
-  int32_t rows;                   // valid rows (<= 128)
-  int32_t row0;                   // first row of the group
-  int32_t xrow0;                  // first row of the leaf (row of X for column 0)
-  int32_t m;                      // leaf rows = D columns
+  int64_t doff[4];                // leaf group: byte offset of each tile's leaf-block part in the pool
+  int32_t ntl;                    // leaf group: tiles in the group (1..4)
+  int32_t rows;                   // valid rows (<= 128); in a V group rows 0 .. rows-1 of its table
+  int32_t row0;                   // leaf group: first row of the group
+  int32_t xrow0;                  // first row of X (K index 0)
+  int32_t m;                      // K extent: leaf rows (leaf group) or valid chunk rows (V group)
+  int32_t vtab;                   // -1: leaf group; else first of its kTcRows entries in the row table
+};
+// One row of a V group: column c of a V chunk (K contiguous, fp32) and the
+// partial row it produces (-1: unused row).
+struct TcVRow {
+  int64_t off;                    // byte offset in the pool of the column at the chunk's first row
+  int32_t prow;                   // partial row, or -1
   int32_t pad_;
 };
 
@@ -133,11 +145,15 @@ struct HandleDev {
   const P2Tile* p2;
   const int32_t* yscat;
   const int2* ritems;             // reduction items: (NodeRed index, row of Y_node), all nodes
-  const TcGroup* tcg;             // tensor-core leaf groups
+  const TcGroup* tcg;             // tensor-core groups (leaf groups, then V groups)
+  const TcVRow* tcv;              // row table of the V groups
+  const VChunk* vch_rest;         // V chunks no V group covers (tensor-core mode)
   const uint8_t* pool;
   int* err;                       // device error word (bounded waits that gave up)
   int32_t n, depth, n_nodes, n_leaves;
   int32_t n_vch, n_nred, n_p2, n_ritems, n_tcg;
+  int32_t n_tcg_leaf;             // leaf groups (the first n_tcg_leaf of tcg)
+  int32_t n_vch_rest;
   int32_t chunk_xrows_max;        // largest real-row span of a V chunk
   int32_t y_rows, p_rows;         // rows of the gathered Y and of the partial buffer
   int32_t max_nq;                 // largest U column count of a tile
@@ -317,14 +333,19 @@ cudaError_t launch_unpack(const uint8_t* pool, const PackTask* tasks, int ntasks
 // holding a 64-bit grid counter whose value is `sync_base` when the launch
 // starts (the launch adds matvec_sync_step to it).
 // ev (may be null): three events, recorded before the launch and twice after.
+// skip_leaf: the tensor-core launch before it has written B = D X for every
+// leaf and the partials of the V chunks its V groups cover; this launch then
+// takes only the other chunks (vch_rest), the reductions and U Y.
 cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx,
                           void* B, int64_t ldb, void* Y, void* partials,
                           unsigned long long* sync, unsigned long long sync_base,
                           cudaStream_t s, cudaEvent_t* ev, int skip_leaf = 0);
-// Leaf products on the tensor cores (fp32 work, kTcMinCols <= nrhs <=
-// kTcMaxCols): B[rows of every leaf] = D_i X[I_i].
-cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const uint8_t* pool, const float* X, int64_t ldx,
-                           int nrhs, float* B, int64_t ldb, int* err, cudaStream_t s);
+// Tensor-core products (fp32 work, kTcMinCols <= nrhs <= kTcMaxCols):
+// B[rows of every leaf group] = D_i X[I_i]; for every V group, the partial
+// rows of its chunks = V_chunk^T X[I] (row-major, nrhs values per row).
+cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
+                           const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials,
+                           int* err, cudaStream_t s);
 // The grid size launch_matvec uses.
 int matvec_grid(const HandleDev& hd);
 // How far one launch advances the grid barrier counter (sync_base of the

@@ -1,11 +1,16 @@
-// Leaf products D_i X[I_i] of Algorithm 3.3 on the fifth-generation tensor
-// cores (tcgen05), for fp32 work with many right-hand sides.
+// Leaf products D_i X[I_i] and the products V_j^T X[I_j] of Algorithm 3.3
+// on the fifth-generation tensor cores (tcgen05), for fp32 work with many
+// right-hand sides.
 //
-// The product kernel (matvec.cu) does the leaf products on CUDA cores; with
-// 16 or more right-hand sides they are a dense contraction worth the tensor
-// cores: per group of up to 128 rows of one leaf,
-//     C (128 x N) = D (128 x m) * X[I_i] (m x N),   N = R rounded up to 16,
-// accumulated in tensor memory (TMEM, fp32).  fp32 is kept by the usual
+// The product kernel (matvec.cu) does both on CUDA cores; with 16 or more
+// right-hand sides they are dense contractions worth the tensor cores.  Per
+// group of up to 128 rows,
+//     C (128 x N) = A (128 x m) * X[I] (m x N),   N = R rounded up to 16,
+// accumulated in tensor memory (TMEM, fp32).  A leaf group's A is up to 128
+// rows of the leaf block D_i (I = I_i), written to B; a V group's A is up to
+// 128 columns of fp32 generators V_j restricted to the rows I of one V
+// chunk (the chunks of one leaf at several levels), written to the chunks'
+// partial rows, which the product kernel then sums per node.  fp32 is kept by the usual
 // three-pass split: every fp32 value x becomes hi + lo with hi = tf32(x)
 // (round to nearest) and lo = tf32(x - hi), and
 //     D X ~ D_hi X_hi + D_hi X_lo + D_lo X_hi,
@@ -174,9 +179,9 @@ __host__ __device__ inline uint32_t tc_smem_bytes(int N) {
 
 template <int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
-leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* __restrict__ pool,
-               const float* __restrict__ X, int64_t ldx, int R, float* __restrict__ B, int64_t ldb,
-               uint32_t tmem_cols, int* err) {
+leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __restrict__ vrows,
+               const uint8_t* __restrict__ pool, const float* __restrict__ X, int64_t ldx, int R,
+               float* __restrict__ B, int64_t ldb, float* __restrict__ partials, uint32_t tmem_cols, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr uint32_t ab = kTcM * kKc * 4, xb = (uint32_t)N * kKc * 4;
@@ -236,11 +241,23 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* _
       const TcGroup* G = groups + g;
       lm = __ldg(&G->m);
       lmp = (lm + 3) & ~3;
-      const int ntl = __ldg(&G->ntl);
+      const int vt = __ldg(&G->vtab);
+      if (vt < 0) {
+        // leaf group: tile i holds rows 32 i .. 32 i + 31, row-major (stride lmp)
+        const int ntl = __ldg(&G->ntl);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        aok[i] = i < ntl;
-        asrc[i] = aok[i] ? pool + __ldg(&G->doff[i]) + ((size_t)rr * lmp + 4 * cg) * 4 : pool;
+        for (int i = 0; i < 4; ++i) {
+          aok[i] = i < ntl;
+          asrc[i] = aok[i] ? pool + __ldg(&G->doff[i]) + ((size_t)rr * lmp + 4 * cg) * 4 : pool;
+        }
+      } else {
+        // V group: row 32 i + rr is one V column, K contiguous
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const TcVRow* e = vrows + vt + 32 * i + rr;
+          aok[i] = __ldg(&e->prow) >= 0;
+          asrc[i] = aok[i] ? pool + __ldg(&e->off) + (size_t)cg * 16 : pool;
+        }
       }
       xbase = X + (int64_t)__ldg(&G->xrow0) * ldx;
     };
@@ -289,6 +306,7 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* _
     for (int u = 0; u < kTcRaw - 1; ++u) issue(u);
     int cg_idx = blockIdx.x, ckc = 0, gcount = 0;   // compute cursor
     int cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
+    int crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
 #pragma unroll 1
     for (int u = 0; u < total; ++u) {
       const int r = u % kTcRaw, b = u & 1;
@@ -303,9 +321,12 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* _
       if (!ok) *(volatile int*)abort_flag = 1;
       // refill the raw stage of chunk u - 1 with chunk u + kTcRaw - 1
       issue(u + kTcRaw - 1);
-      // A: split into hi and lo
+      // A: split into hi and lo (rows past the group's valid rows keep
+      // whatever the buffer held: they only reach accumulator rows that the
+      // epilogue does not write)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
+        if (32 * i + rr >= crows) continue;
         const uint32_t o = so0 + 4096u * i;
         const uint4 v = lds16(ra + o);
         uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
@@ -340,14 +361,25 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* _
           const bool okw = bar_wait(acc_ready, (uint32_t)(gcount & 1), err, 23) && !*(volatile int*)abort_flag;
           tc_fence_after();
           const int row = 32 * warp + lane;
-          const int rows = __ldg(&G->rows), row0 = __ldg(&G->row0);
-          float* brow = B + (int64_t)(row0 + row) * ldb;
-          const bool vec = (R == N) && (ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+          const int vt = __ldg(&G->vtab);
+          bool rok;
+          float* brow;
+          bool vec;
+          if (vt < 0) {
+            rok = row < __ldg(&G->rows);
+            brow = B + (int64_t)(__ldg(&G->row0) + row) * ldb;
+            vec = (R == N) && (ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+          } else {
+            const int pr = __ldg(&vrows[vt + row].prow);
+            rok = pr >= 0;
+            brow = partials + (int64_t)max(pr, 0) * R;
+            vec = (R == N) && ((reinterpret_cast<uintptr_t>(partials) & 15) == 0);
+          }
 #pragma unroll
           for (int c0 = 0; c0 < N; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-            if (okw && row < rows) {
+            if (okw && rok) {
               if (vec) {
 #pragma unroll
                 for (int j = 0; j < 16; j += 4)
@@ -364,6 +396,7 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const uint8_t* _
         ckc = 0;
         cg_idx += gridDim.x;
         cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
+        crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
         ++gcount;
         // the accumulator may be overwritten once the epilogue has read it
         asm volatile("bar.sync 2, %0;" ::"r"(kConvThreads + 32) : "memory");
@@ -430,8 +463,9 @@ size_t leaf_tc_smem(int N) { return tc_smem_bytes(N); }
 
 namespace {
 template <int N>
-cudaError_t launch_n(const TcGroup* groups, int ngroups, const uint8_t* pool, const float* X, int64_t ldx,
-                     int nrhs, float* B, int64_t ldb, int* err, cudaStream_t s) {
+cudaError_t launch_n(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
+                     const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials, int* err,
+                     cudaStream_t s) {
   uint32_t cols = 32;
   while (cols < (uint32_t)N) cols <<= 1;
   const size_t smem = leaf_tc_smem(N);
@@ -442,21 +476,23 @@ cudaError_t launch_n(const TcGroup* groups, int ngroups, const uint8_t* pool, co
     smem_set = smem;
   }
   const int grid = std::min(ngroups, tc_sms());
-  leaf_tc_kernel<N><<<grid, kTcThreads, smem, s>>>(groups, ngroups, pool, X, ldx, nrhs, B, ldb, cols, err);
+  leaf_tc_kernel<N><<<grid, kTcThreads, smem, s>>>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials,
+                                                    cols, err);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const uint8_t* pool, const float* X, int64_t ldx,
-                           int nrhs, float* B, int64_t ldb, int* err, cudaStream_t s) {
+cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
+                           const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials,
+                           int* err, cudaStream_t s) {
   if (ngroups == 0 || nrhs == 0) return cudaSuccess;
   const int N = (nrhs + 15) / 16 * 16;
   if (N < 16 || N > kTcMaxCols) return cudaErrorInvalidValue;
   switch (N) {
-    case 16: return launch_n<16>(groups, ngroups, pool, X, ldx, nrhs, B, ldb, err, s);
-    case 32: return launch_n<32>(groups, ngroups, pool, X, ldx, nrhs, B, ldb, err, s);
-    case 48: return launch_n<48>(groups, ngroups, pool, X, ldx, nrhs, B, ldb, err, s);
-    default: return launch_n<64>(groups, ngroups, pool, X, ldx, nrhs, B, ldb, err, s);
+    case 16: return launch_n<16>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    case 32: return launch_n<32>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    case 48: return launch_n<48>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    default: return launch_n<64>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
   }
 }
 

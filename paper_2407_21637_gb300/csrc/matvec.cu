@@ -3,28 +3,34 @@
 // Algorithm 3.3 walks the levels and adds U_{2i-1}(V_{2i}^T x_{2i}) and
 // U_{2i}(V_{2i-1}^T x_{2i-1}) into b, then the leaf products D_i x_i.  Here
 // the level loop is flattened into one persistent kernel (one CTA per SM,
-// cooperative launch so that all CTAs are co-resident) with three stages per
-// CTA:
+// cooperative launch so that all CTAs are co-resident) with these stages:
 //
-//  phase A  Y_j = V_j^T X[I_j] for every node j of every level, in chunks of
-//           up to 512 rows; each Y_j is written into the gathered-Y block of
-//           every leaf below the sibling of j;
+//  phase A  every warp of the grid takes V chunks (up to 256 rows of one
+//           node V_j) and writes the chunk's part of V_j^T X[I_j] to its
+//           partial rows, loading V and X directly;
+//  reduce   after a grid counter shows every chunk done: Y_j = the sum of
+//           its chunk partials in chunk order, scaled, written into the
+//           gathered-Y block of every leaf below the sibling of j (three
+//           reducer warps per CTA; the items are dealt across the CTAs);
 //  pass 1   for every 32-row tile of a leaf i: D_i[rows, :] X[I_i], which
-//           does not depend on phase A;
-//  pass 2   for every tile: B[rows] = (pass 1) + sum_k U_{a_k}[rows, :]
-//           Y_{a_k ^ 1}, a_k the level-k ancestor of leaf i.
+//           does not depend on phase A (a producer warp streams the tiles'
+//           leaf blocks and X rows through a ring of shared-memory stages
+//           with cp.async.bulk, completion on mbarriers) -- it overlaps the
+//           reductions;
+//  pass 2   after a second grid counter: for every tile, B[rows] = (pass 1)
+//           + sum_k U_{a_k}[rows, :] Y_{a_k ^ 1}, a_k the level-k ancestor
+//           of leaf i (one warp per tile, U rows by a bulk copy into the
+//           warp's slice of shared memory).
+//
+// With fp32 work and 16 or more right-hand sides the leaf products and the
+// fp32 V chunks go to the tensor cores first (leaf_tc.cu); this kernel then
+// runs with skip_leaf: no pass 1, phase A only for the chunks left over,
+// and the consumer warps help with the reductions.
 //
 // Each output row is written once, with a fixed summation order, so the
-// product is bitwise reproducible.  A producer warp per CTA streams the V
-// chunks, the tiles' leaf blocks and then the tiles' U rows and gathered-Y
-// blocks into a ring of shared-memory stages with bulk asynchronous copies
-// (cp.async.bulk, completion on an mbarrier); sixteen consumer warps
-// multiply out of shared memory.  Only the producer waits for the other CTAs
-// (a grid counter that every CTA increments after phase A), just before it
-// copies the first gathered-Y block, so phase A of the slowest CTA overlaps
-// pass 1 everywhere.  Every wait gives up after two seconds; a wait that
-// gives up records an error code in the handle's error word and the CTA
-// drains the copies it issued and returns.
+// product is bitwise reproducible.  Every wait gives up after two seconds; a
+// wait that gives up records an error code in the handle's error word and
+// the CTA drains the copies it issued and returns.
 #include <algorithm>
 #include <type_traits>
 
@@ -473,8 +479,12 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   //      X directly (a chunk is at most kChunkRows rows of one node) ----
   // chunks are dealt to the CTAs in turn (warp w of CTA c starts at chunk
   // w * grid + c), so the wide top-level chunks spread over all SMs
-  for (int c = warp * G + blockIdx.x; c < hd.n_vch; c += G * kCWarps) {
-    const VChunk& ch = hd.vch[c];
+  // (with skip_leaf the tensor-core launch has done the chunks its V groups
+  // cover: only the rest are left)
+  const VChunk* const vchs = skip_leaf ? hd.vch_rest : hd.vch;
+  const int n_vchs = skip_leaf ? hd.n_vch_rest : hd.n_vch;
+  for (int c = warp * G + blockIdx.x; c < n_vchs; c += G * kCWarps) {
+    const VChunk& ch = vchs[c];
     const int rV = __ldg(&ch.rV), poff = __ldg(&ch.poff), nseg = __ldg(&ch.nseg), tier = __ldg(&ch.tier);
     const int colbytes = __ldg(&ch.colbytes);
     const uint8_t* vbase = hd.pool + __ldg(&ch.off);

@@ -27,14 +27,14 @@ pytestmark = pytest.mark.gpu
 TIERS = ("fp64", "fp32", "bf16", "fp16", "e4m3")
 
 
-def _setup(n, depth, eps, spec, seed):
+def _setup(n, depth, eps, spec, seed, tiers=TIERS):
     from paper_2407_21637_gb300 import HodlrMatrix
     pts = synth.uniform_points_1d(n, seed)
     h = C.compress(pts, spec, n, depth, eps)
-    C.assign_precisions(h, eps, "fp32", TIERS, norms="factors")
+    C.assign_precisions(h, eps, "fp32", tiers, norms="factors")
     C.store_all(h)
     ranks, U, V, D = oracle_to_abi(h)
-    g = HodlrMatrix.from_factors(n, depth, ranks, U, V, D, eps=eps, work="fp32", tiers=TIERS, max_nrhs=256)
+    g = HodlrMatrix.from_factors(n, depth, ranks, U, V, D, eps=eps, work="fp32", tiers=tiers, max_nrhs=256)
     return h, g
 
 
@@ -56,6 +56,25 @@ def test_tc_parity(n, depth, R):
     tol = _tol_tc(h, X64, ref)
     assert np.all(err <= tol), float(np.max(err / tol))
     assert np.linalg.norm(B - ref) <= 1e-5 * np.linalg.norm(ref)
+    g.close()
+
+
+@pytest.mark.parametrize("n,depth", [(4096, 4), (2000, 3), (1500, 2)])
+@pytest.mark.parametrize("R", [16, 64])
+def test_tc_fp32_generators(n, depth, R):
+    """Every generator stored in fp32, so every V chunk that covers one run
+    of rows goes to the tensor cores in a V group: all of them for n = 4096
+    and 2000 (256-row padded leaves), and for n = 1500 (375-row leaves) the
+    256- and 119-row pieces of the leaves, while the chunks that span two
+    leaves stay on the CUDA cores."""
+    spec = synth.KernelSpec(K.GAUSS, len2=0.01, diag=1e-2)
+    h, g = _setup(n, depth, 1e-6, spec, 5, tiers=("fp32",))
+    X = synth.rhs_normal(n, R, 900 + R, np.float32)
+    B = g.matvec(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    X64 = X.astype(np.float64)
+    ref = M.hodlr_matvec(h, X64)
+    tol = _tol_tc(h, X64, ref)
+    assert np.all(np.abs(B - ref) <= tol), float(np.max(np.abs(B - ref) / tol))
     g.close()
 
 
