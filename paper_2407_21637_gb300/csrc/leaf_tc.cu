@@ -10,26 +10,28 @@
 // rows of the leaf block D_i (I = I_i), written to B; a V group's A is up to
 // 128 columns of fp32 generators V_j restricted to the rows I of one V
 // chunk (the chunks of one leaf at several levels), written to the chunks'
-// partial rows, which the product kernel then sums per node.  fp32 is kept by the usual
-// three-pass split: every fp32 value x becomes hi + lo with hi = tf32(x)
-// (round to nearest) and lo = tf32(x - hi), and
-//     D X ~ D_hi X_hi + D_hi X_lo + D_lo X_hi,
-// whose error per product is at most about 3 * 2^-22 |d| |x| (the dropped
-// D_lo X_lo term and the rounding of the lo parts), far inside the
-// elementwise bound the product is tested against.
+// partial rows, which the product kernel then sums per node.  fp32 is kept
+// by splitting every fp32 value x into hi + lo with hi = tf32(x) (round to
+// nearest) and lo = tf32(x - hi); per K step two MMAs of width 2N,
+//     A_hi [X_hi | X_lo] + A_lo [X_hi | X_lo],
+// give all four partial products in two accumulator halves that the
+// epilogue adds.  The error per product is at most about 2 * 2^-22 |a| |x|
+// (the rounding of the two lo parts), far inside the elementwise bound the
+// product is tested against.
 //
-// Per CTA (persistent, one per SM): eight converter warps keep a ring of
-// two to four stages in flight with cp.async: a K-chunk of 32 columns of D
-// for 128 rows (placed directly in the tensor cores' K-major layout with the
-// 128-byte swizzle) and the matching 32 rows of X.  Once a chunk has landed
-// they split it in shared memory (D's hi part over the raw values, lo beside
-// it; X transposed into N x 32 hi and lo tiles); one thread issues the MMAs
-// (tcgen05.mma.kind::tf32, A and B from shared-memory descriptors) and
-// commits them to the stage's mbarrier, which frees the stage for the next
-// copies.  After a group's last chunk the four epilogue warps read the
-// accumulator (tcgen05.ld) and write B.  Every wait is bounded (two seconds)
-// and records an error code; the CTA always frees its tensor memory before
-// it exits.
+// Per CTA (persistent, one per SM): sixteen converter warps keep a ring of
+// six stages with cp.async: a K-chunk of 32 columns of A for 128 rows
+// (placed in the 128-byte-swizzled K-major layout) and the matching 32 rows
+// of X.  Once a chunk has landed they split it: A's hi and lo parts go to
+// tensor memory (tcgen05.st, lane = row), X is transposed into N x 32 hi
+// and lo tiles in shared memory (two operand buffers each).  One thread
+// issues the MMAs (tcgen05.mma.kind::tf32, A from tensor memory, B from a
+// shared-memory descriptor) and commits them to the buffer's mbarrier,
+// which frees it for the next chunk.  Groups alternate between two
+// accumulators in TMEM, so that four epilogue warps (one per TMEM lane
+// quadrant) read one group's result (tcgen05.ld) and write it out while the
+// next group accumulates.  Every wait is bounded (two seconds) and records
+// an error code; the CTA always frees its tensor memory before it exits.
 #include <algorithm>
 
 #include "hodlr_internal.cuh"
@@ -38,9 +40,10 @@ namespace hodlr {
 
 namespace {
 
-constexpr int kConvWarps = 8;
+constexpr int kConvWarps = 16;
 constexpr int kConvThreads = 32 * kConvWarps;
-constexpr int kTcThreads = kConvThreads + 32;   // + the MMA warp
+constexpr int kEpiWarps = 4;                    // one per TMEM lane quadrant
+constexpr int kTcThreads = kConvThreads + 32 + 32 * kEpiWarps;   // converters, the MMA warp, epilogue
 constexpr int kTcM = 128;                       // rows per group (MMA M)
 constexpr int kKc = 32;                         // K-chunk: 32 fp32 = one 128-byte swizzle row
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
@@ -112,15 +115,24 @@ __device__ __forceinline__ void sts4(uint32_t a, uint32_t x, uint32_t y, uint32_
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (+)= A B, A in tensor memory (128 lanes = rows, one tf32 per column), B from
+// a shared-memory descriptor.
+__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// 8 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                : "memory");
@@ -166,13 +178,21 @@ __device__ __forceinline__ float lds1f(uint32_t a) {
 }
 
 // Shared memory (every part 1024-byte aligned):
-//  raw ring, kTcRaw stages: A (128 x 32 fp32 of D, placed by cp.async in the
-//    swizzled K-major layout) and X (32 x N fp32, row-major as loaded);
-//  two operand buffers: A_hi, A_lo (128 x 32 tf32) and B_hi, B_lo (X^T,
-//    N x 32 tf32), all K-major with the 128-byte swizzle.
-constexpr int kTcRaw = 4;
+//  raw ring, kTcRaw stages: A (128 x 32 fp32, placed by cp.async in the
+//    128-byte-swizzled K-major layout) and X (32 x N fp32, row-major as
+//    loaded);
+//  two operand buffers B_hi, B_lo (X^T, N x 32 tf32, K-major, 128-byte
+//    swizzle).
+// Tensor memory (512 columns): two accumulators of 2N columns (columns
+// 128 a: the products with X_hi in the first N, with X_lo in the next N)
+// and two A operand buffers (columns kTmemA + 64 b: A_hi in 32 columns,
+// A_lo in the next 32; lane = row of A).
+constexpr int kTcRaw = 6;
+constexpr uint32_t kTmemAcc = 128;
+constexpr uint32_t kTmemA = 2 * kTmemAcc;
+constexpr uint32_t kTmemCols = 512;
 __host__ __device__ inline uint32_t tc_raw_bytes(int N) { return (uint32_t)kTcM * kKc * 4 + (uint32_t)N * kKc * 4; }
-__host__ __device__ inline uint32_t tc_op_bytes(int N) { return 2u * kTcM * kKc * 4 + 2u * (uint32_t)N * kKc * 4; }
+__host__ __device__ inline uint32_t tc_op_bytes(int N) { return 2u * (uint32_t)N * kKc * 4; }
 __host__ __device__ inline uint32_t tc_smem_bytes(int N) {
   return 1024 + kTcRaw * tc_raw_bytes(N) + 2 * tc_op_bytes(N) + 256;
 }
@@ -185,22 +205,25 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr uint32_t ab = kTcM * kKc * 4, xb = (uint32_t)N * kKc * 4;
-  constexpr uint32_t rb = ab + xb, ob = 2 * ab + 2 * xb;
+  constexpr uint32_t rb = ab + xb, ob = 2 * xb;
+  static_assert(2 * N <= (int)kTmemAcc, "accumulator wider than its TMEM slot");
   const uint32_t raw0 = su32(base), op0 = raw0 + kTcRaw * rb;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTcRaw * rb + 2 * ob);
   uint64_t* conv_done = bars;          // [2], kConvThreads arrivals
   uint64_t* mma_done = bars + 2;       // [2], one commit
-  uint64_t* acc_ready = bars + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 5);
-  int* abort_flag = reinterpret_cast<int*>(bars + 6);
+  uint64_t* acc_full = bars + 4;       // [2] accumulator buffers, one commit
+  uint64_t* acc_empty = bars + 6;      // [2], kEpiWarps arrivals
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  int* abort_flag = reinterpret_cast<int*>(bars + 9);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) {
       bar_init(&conv_done[b], kConvThreads);
       bar_init(&mma_done[b], 1);
+      bar_init(&acc_full[b], 1);
+      bar_init(&acc_empty[b], kEpiWarps);
     }
-    bar_init(acc_ready, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -214,7 +237,7 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t idesc = idesc_tf32(kTcM, N);
+  constexpr uint32_t idesc = idesc_tf32(kTcM, 2 * N);   // B = [X_hi | X_lo]
   const bool x16 = (ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
   // this CTA's chunks, in order: (group, K-chunk)
@@ -223,18 +246,27 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
 
   if (warp < kConvWarps) {
     const int t = threadIdx.x;
-    // fixed per thread: A pieces (row rr + 32 i = tile i, 16-byte group cg),
-    // X pieces (row kx + 256 / (N / 4) * j, columns nx .. nx + 3) and B
-    // pieces (row nb, 16-byte group kb + 256 / N * j)
+    // fixed per thread: A pieces (row rr + kAR i, 16-byte group cg),
+    // X pieces (piece p = t + kConvThreads j: row p / (N / 4), columns
+    // 4 (p % (N / 4)) .. + 3) and B pieces (row p % N, 16-byte group p / N)
     constexpr int n4 = N / 4;
     constexpr int XP = (kKc * n4 + kConvThreads - 1) / kConvThreads;   // X pieces per thread
     constexpr int BP = (N * (kKc / 4) + kConvThreads - 1) / kConvThreads;
+    constexpr int kAR = kConvThreads / 8;   // A rows per pass of all converter threads
+    constexpr int kAP = kTcM / kAR;         // A pieces per thread
+    static_assert(kAP * kAR == kTcM && kAR % 32 == 0, "converter threads must tile the 128 A rows");
     const int rr = t >> 3, cg = t & 7;
-    const uint32_t so0 = sw128(rr, cg);   // + 4096 * i for tile i
+    const uint32_t so0 = sw128(rr, cg);   // + kAR * 128 * i for piece i
+    // A split: warp w takes TMEM lanes 32 (w % 4) .. + 31 (row = lane) and
+    // columns 8 (w / 4) .. + 7 of the chunk
+    static_assert(kConvWarps == 16, "four warps per TMEM lane quadrant");
+    const int aq = warp & 3, akq = warp >> 2;
+    const int arow = 32 * aq + lane;
+    const uint32_t alane = (uint32_t)(32 * aq) << 16;
     // load cursor state (per group)
     int lg = blockIdx.x, lkc = 0;
-    const uint8_t* asrc[4];
-    bool aok[4];
+    const uint8_t* asrc[kAP];
+    bool aok[kAP];
     int lm = 0, lmp = 0;
     const float* xbase = X;
     auto load_group = [&](int g) {
@@ -243,18 +275,19 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
       lmp = (lm + 3) & ~3;
       const int vt = __ldg(&G->vtab);
       if (vt < 0) {
-        // leaf group: tile i holds rows 32 i .. 32 i + 31, row-major (stride lmp)
+        // leaf group: tile r / 32 holds rows r, row-major (stride lmp)
         const int ntl = __ldg(&G->ntl);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          aok[i] = i < ntl;
-          asrc[i] = aok[i] ? pool + __ldg(&G->doff[i]) + ((size_t)rr * lmp + 4 * cg) * 4 : pool;
+        for (int i = 0; i < kAP; ++i) {
+          const int r = rr + kAR * i;
+          aok[i] = (r >> 5) < ntl;
+          asrc[i] = aok[i] ? pool + __ldg(&G->doff[r >> 5]) + ((size_t)(r & 31) * lmp + 4 * cg) * 4 : pool;
         }
       } else {
-        // V group: row 32 i + rr is one V column, K contiguous
+        // V group: row r is one V column, K contiguous
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const TcVRow* e = vrows + vt + 32 * i + rr;
+        for (int i = 0; i < kAP; ++i) {
+          const TcVRow* e = vrows + vt + rr + kAR * i;
           aok[i] = __ldg(&e->prow) >= 0;
           asrc[i] = aok[i] ? pool + __ldg(&e->off) + (size_t)cg * 16 : pool;
         }
@@ -268,9 +301,9 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
         const uint32_t ra = raw0 + (uint32_t)(u % kTcRaw) * rb, rx = ra + ab;
         const bool kin = 4 * cg + k0 < lmp;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < kAP; ++i) {
           const bool ok = aok[i] && kin;
-          cp_async16(ra + so0 + 4096u * i, ok ? (const void*)(asrc[i] + (size_t)k0 * 4) : (const void*)pool,
+          cp_async16(ra + so0 + (uint32_t)(kAR * 128) * i, ok ? (const void*)(asrc[i] + (size_t)k0 * 4) : (const void*)pool,
                      ok ? 16u : 0u);
         }
 #pragma unroll
@@ -304,7 +337,7 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
     // prologue: chunks 0 .. kTcRaw - 2 in flight
 #pragma unroll 1
     for (int u = 0; u < kTcRaw - 1; ++u) issue(u);
-    int cg_idx = blockIdx.x, ckc = 0, gcount = 0;   // compute cursor
+    int cg_idx = blockIdx.x, ckc = 0;   // compute cursor
     int cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
     int crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
 #pragma unroll 1
@@ -312,30 +345,33 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
       const int r = u % kTcRaw, b = u & 1;
       const uint32_t ra = raw0 + (uint32_t)r * rb, rx = ra + ab;
       const uint32_t oa = op0 + (uint32_t)b * ob;
-      // chunk u's copies have landed (chunks u + 1 and u + 2 may be pending)
+      // chunk u's copies have landed (the kTcRaw - 2 after it may be pending)
       cp_async_wait<kTcRaw - 2>();
       bar_conv();   // everybody's copies; everybody is done with raw stage (u - 1) % kTcRaw
       // the operand buffer of chunk u - 2 is free once its MMAs are done
       bool ok = !*(volatile int*)abort_flag;
       if (ok && u >= 2) ok = bar_wait(&mma_done[b], (uint32_t)(((u >> 1) - 1) & 1), err, 21);
       if (!ok) *(volatile int*)abort_flag = 1;
+      tc_fence_after();
       // refill the raw stage of chunk u - 1 with chunk u + kTcRaw - 1
       issue(u + kTcRaw - 1);
-      // A: split into hi and lo (rows past the group's valid rows keep
-      // whatever the buffer held: they only reach accumulator rows that the
-      // epilogue does not write)
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        if (32 * i + rr >= crows) continue;
-        const uint32_t o = so0 + 4096u * i;
-        const uint4 v = lds16(ra + o);
-        uint32_t h0, l0, h1, l1, h2, l2, h3, l3;
-        split(__uint_as_float(v.x), h0, l0);
-        split(__uint_as_float(v.y), h1, l1);
-        split(__uint_as_float(v.z), h2, l2);
-        split(__uint_as_float(v.w), h3, l3);
-        sts4(oa + o, h0, h1, h2, h3);
-        sts4(oa + ab + o, l0, l1, l2, l3);
+      // A: split into hi and lo, into tensor memory (a quadrant past the
+      // group's valid rows is skipped; rows past them in a quadrant reach
+      // only accumulator rows that the epilogue does not write)
+      if (32 * aq < crows) {
+        const uint4 v0 = lds16(ra + sw128(arow, 2 * akq)), v1 = lds16(ra + sw128(arow, 2 * akq + 1));
+        uint32_t h[8], l[8];
+        split(__uint_as_float(v0.x), h[0], l[0]);
+        split(__uint_as_float(v0.y), h[1], l[1]);
+        split(__uint_as_float(v0.z), h[2], l[2]);
+        split(__uint_as_float(v0.w), h[3], l[3]);
+        split(__uint_as_float(v1.x), h[4], l[4]);
+        split(__uint_as_float(v1.y), h[5], l[5]);
+        split(__uint_as_float(v1.z), h[6], l[6]);
+        split(__uint_as_float(v1.w), h[7], l[7]);
+        const uint32_t ta = tmem + alane + kTmemA + 64u * (uint32_t)b + 8u * (uint32_t)akq;
+        tmem_st8(ta, h);
+        tmem_st8(ta + 32, l);
       }
       // B = X^T: thread (n, k-group of 4), consecutive threads take consecutive n
 #pragma unroll
@@ -347,97 +383,116 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
 #pragma unroll
           for (int e = 0; e < 4; ++e) split(lds1f(rx + (uint32_t)(((4 * kg + e) * N + n) * 4)), h[e], l[e]);
           const uint32_t o = sw128(n, kg);
-          sts4(oa + 2 * ab + o, h[0], h[1], h[2], h[3]);
-          sts4(oa + 2 * ab + xb + o, l[0], l[1], l[2], l[3]);
+          sts4(oa + o, h[0], h[1], h[2], h[3]);
+          sts4(oa + xb + o, l[0], l[1], l[2], l[3]);
         }
       }
-      // generic-proxy stores -> visible to the tensor cores (async proxy)
+      // TMEM stores complete, generic-proxy stores -> visible to the tensor
+      // cores (async proxy)
+      tmem_wait_st();
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
       bar_arrive(&conv_done[b]);
-      // end of a group: epilogue by warps 0..3 (one TMEM lane quadrant each)
       if (++ckc * kKc >= cm) {
-        if (warp < 4) {
-          const TcGroup* G = groups + cg_idx;
-          const bool okw = bar_wait(acc_ready, (uint32_t)(gcount & 1), err, 23) && !*(volatile int*)abort_flag;
-          tc_fence_after();
-          const int row = 32 * warp + lane;
-          const int vt = __ldg(&G->vtab);
-          bool rok;
-          float* brow;
-          bool vec;
-          if (vt < 0) {
-            rok = row < __ldg(&G->rows);
-            brow = B + (int64_t)(__ldg(&G->row0) + row) * ldb;
-            vec = (R == N) && (ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
-          } else {
-            const int pr = __ldg(&vrows[vt + row].prow);
-            rok = pr >= 0;
-            brow = partials + (int64_t)max(pr, 0) * R;
-            vec = (R == N) && ((reinterpret_cast<uintptr_t>(partials) & 15) == 0);
-          }
-#pragma unroll
-          for (int c0 = 0; c0 < N; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-            if (okw && rok) {
-              if (vec) {
-#pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                  *reinterpret_cast<float4*>(brow + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-              } else {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                  if (c0 + j < R) brow[c0 + j] = v[j];
-              }
-            }
-          }
-          tc_fence_before();
-        }
         ckc = 0;
         cg_idx += gridDim.x;
         cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
         crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
-        ++gcount;
-        // the accumulator may be overwritten once the epilogue has read it
-        asm volatile("bar.sync 2, %0;" ::"r"(kConvThreads + 32) : "memory");
       }
     }
     cp_async_wait<0>();
-  } else {
-    // ================= MMA issuer (warp kConvWarps) =================
-    int ckc = 0, cg_idx = blockIdx.x;
+  } else if (warp == kConvWarps) {
+    // ================= MMA issuer =================
+    // group number gc accumulates into TMEM columns kTmemAcc (gc & 1); per
+    // 8-wide K step, A_hi [X_hi | X_lo] + A_lo [X_hi | X_lo]
+    int ckc = 0, cg_idx = blockIdx.x, gc = 0;
     int cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
 #pragma unroll 1
     for (int u = 0; u < total; ++u) {
       const int b = u & 1;
+      const uint32_t acc = tmem + (uint32_t)(gc & 1) * kTmemAcc;
+      const bool last = (ckc + 1) * kKc >= cm;
       if (lane == 0) {
-        if (bar_wait(&conv_done[b], (uint32_t)((u >> 1) & 1), err, 22) && !*(volatile int*)abort_flag) {
+        bool ok = !*(volatile int*)abort_flag;
+        // a group's first chunk: its accumulator buffer must have been read
+        if (ok && ckc == 0 && gc >= 2) ok = bar_wait(&acc_empty[gc & 1], (uint32_t)(((gc >> 1) - 1) & 1), err, 24);
+        if (ok) ok = bar_wait(&conv_done[b], (uint32_t)((u >> 1) & 1), err, 22);
+        if (ok && !*(volatile int*)abort_flag) {
           tc_fence_after();
           const uint32_t oa = op0 + (uint32_t)b * ob;
-          const uint64_t ah = desc_sw128(oa), al = desc_sw128(oa + ab);
-          const uint64_t bh = desc_sw128(oa + 2 * ab), bl = desc_sw128(oa + 2 * ab + xb);
+          const uint32_t ah = tmem + kTmemA + 64u * (uint32_t)b, al = ah + 32;
+          const uint64_t bd = desc_sw128(oa);   // 2N rows: X_hi^T, then X_lo^T
 #pragma unroll
           for (int ks = 0; ks < kKc / 8; ++ks) {
             const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 8 tf32 = 32 bytes along K
-            mma_tf32(tmem, ah + adv, bh + adv, idesc, (ckc > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(tmem, ah + adv, bl + adv, idesc, 1u);
-            mma_tf32(tmem, al + adv, bh + adv, idesc, 1u);
+            const uint32_t ac = (uint32_t)(ks * 8);          // 8 tf32 = 8 TMEM columns
+            mma_tf32_tmem_a(acc, ah + ac, bd + adv, idesc, (ckc > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32_tmem_a(acc, al + ac, bd + adv, idesc, 1u);
           }
         } else {
           *(volatile int*)abort_flag = 1;
         }
         mma_commit(&mma_done[b]);
+        if (last) mma_commit(&acc_full[gc & 1]);
       }
       __syncwarp();
-      if (++ckc * kKc >= cm) {
-        if (lane == 0) mma_commit(acc_ready);
+      if (last) {
         ckc = 0;
         cg_idx += gridDim.x;
         cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
-        // wait for the epilogue before the next group overwrites the accumulator
-        asm volatile("bar.sync 2, %0;" ::"r"(kConvThreads + 32) : "memory");
-        tc_fence_after();
+        ++gc;
+      } else {
+        ++ckc;
       }
+    }
+  } else {
+    // ================= epilogue: accumulator -> B or partial rows =================
+    // warp kConvWarps + 1 + e reads TMEM lanes 32 q .. 32 q + 31, q = warp % 4
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    int gc = 0;
+#pragma unroll 1
+    for (int g = blockIdx.x; g < ngroups; g += gridDim.x, ++gc) {
+      const TcGroup* G = groups + g;
+      const bool okw = bar_wait(&acc_full[gc & 1], (uint32_t)((gc >> 1) & 1), err, 23) && !*(volatile int*)abort_flag;
+      tc_fence_after();
+      const int vt = __ldg(&G->vtab);
+      bool rok;
+      float* brow;
+      bool vec;
+      if (vt < 0) {
+        rok = row < __ldg(&G->rows);
+        brow = B + (int64_t)(__ldg(&G->row0) + row) * ldb;
+        vec = (R == N) && (ldb % 4 == 0) && ((reinterpret_cast<uintptr_t>(B) & 15) == 0);
+      } else {
+        const int pr = __ldg(&vrows[vt + row].prow);
+        rok = pr >= 0;
+        brow = partials + (int64_t)max(pr, 0) * R;
+        vec = (R == N) && ((reinterpret_cast<uintptr_t>(partials) & 15) == 0);
+      }
+      const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(gc & 1) * kTmemAcc;
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16], w[16];
+        tmem_ld16(acc + (uint32_t)c0, v);
+        tmem_ld16(acc + (uint32_t)(N + c0), w);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += w[j];
+        if (okw && rok) {
+          if (vec) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(brow + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < R) brow[c0 + j] = v[j];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&acc_empty[gc & 1]);
     }
   }
   __syncthreads();
@@ -466,8 +521,7 @@ template <int N>
 cudaError_t launch_n(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
                      const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials, int* err,
                      cudaStream_t s) {
-  uint32_t cols = 32;
-  while (cols < (uint32_t)N) cols <<= 1;
+  const uint32_t cols = kTmemCols;   // two accumulators, two A operand buffers
   const size_t smem = leaf_tc_smem(N);
   static size_t smem_set = 0;   // per instantiation
   if (smem > smem_set) {

@@ -4,10 +4,11 @@ factors, fp64), for ragged leaves (row counts that are not multiples of 32,
 128 or of the 32-column K-chunks), column counts that are not multiples of
 16 or 4, strided X and B, batches of columns, and bitwise repeatability.
 
-The bound: the leaf products are three tf32 products (hi*hi + hi*lo +
-lo*hi of the split fp32 values), so each product carries up to about
-3 * 2^-22 = 12u relative error, and the tensor core's fp32 accumulation is
-allowed 2u per addition: |b_gpu - b| <= (gamma_N(2u) + 14u) g + u|b| with
+The bound: the tensor-core products are sums of tf32 products of the split
+fp32 values (hi + lo, both parts of both factors), so each product carries
+up to about 2 * 2^-22 = 8u relative error from the rounding of the lo
+parts; 14u is allowed, and the tensor core's fp32 accumulation 2u per
+addition: |b_gpu - b| <= (gamma_N(2u) + 14u) g + u|b| with
 g = |U|(|V|^T|x|) + |D||x| and N the longest accumulation chain.
 """
 import numpy as np
