@@ -160,11 +160,19 @@ struct Lanes {
   static constexpr int RTA = 8;                 // V columns per phase-A pass
 };
 
-// CPL consecutive values of a row (8- or 16-byte aligned when CPL = 2).
+// CPL consecutive values of a row (8- or 16-byte aligned when CPL = 2, 16
+// when CPL = 4, fp32 only).
 template <typename W, int CPL>
 __device__ __forceinline__ void load_cols(const W* p, bool global, W (&v)[CPL]) {
+  static_assert(CPL <= 2 || (CPL == 4 && sizeof(W) == 4), "four columns per lane in fp32 only");
   if constexpr (CPL == 1) {
     v[0] = global ? __ldg(p) : *p;
+  } else if constexpr (CPL == 4) {
+    const float4 t = global ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
   } else if constexpr (sizeof(W) == 4) {
     const float2 t = global ? __ldg(reinterpret_cast<const float2*>(p)) : *reinterpret_cast<const float2*>(p);
     v[0] = t.x;
@@ -179,6 +187,8 @@ template <typename W, int CPL>
 __device__ __forceinline__ void store_cols(W* p, const W (&v)[CPL]) {
   if constexpr (CPL == 1) {
     *p = v[0];
+  } else if constexpr (CPL == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   } else if constexpr (sizeof(W) == 4) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
   } else {
@@ -230,6 +240,8 @@ template <typename W, int CPL>
 __device__ __forceinline__ void sld_cols(uint32_t a, W (&v)[CPL]) {
   if constexpr (CPL == 1) {
     v[0] = sld<W>(a);
+  } else if constexpr (CPL == 4) {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]) : "r"(a));
   } else if constexpr (sizeof(W) == 4) {
     asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v[0]), "=f"(v[1]) : "r"(a));
   } else {
@@ -346,19 +358,25 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 
   // ---- node reductions: Y_node[a, :] = invs * sum of its chunk partials
   //      (each lane sums the partials lane, lane + 32, ... in order, then a
-  //      fixed butterfly), written to the node's gathered-Y targets.  The
-  //      items are sorted heaviest first and dealt to the CTAs in turn (warp
-  //      w of CTA c starts at item w * grid + c) so that no SM gets several
-  //      heavy ones; a warp takes items first, first + stride, ... ----
+  //      fixed butterfly), written to the node's gathered-Y targets.  A work
+  //      unit is one item (node, row a) and one block of kMaxColsLane
+  //      columns, so that the items with the most partials do not hold up
+  //      the grid with a long chain of loads.  The items are sorted heaviest
+  //      first and the units dealt to the CTAs in turn (warp w of CTA c
+  //      starts at unit w * grid + c) so that no SM gets several heavy ones;
+  //      a warp takes units first, first + stride, ... ----
+  const int ncb = (R + kMaxColsLane - 1) / kMaxColsLane;
   auto reduce_items = [&](int first, int stride) {
-    for (int it = first; it < hd.n_ritems; it += stride) {
+    for (int wu = first; wu < hd.n_ritems * ncb; wu += stride) {
+      const int it = wu / ncb;
       const int2 ri = __ldg(hd.ritems + it);
       const NodeRed* nrp = hd.nred + ri.x;
       const int P = __ldg(&nrp->nparts), rV = __ldg(&nrp->rV), poff0 = __ldg(&nrp->poff0);
       const int y0 = __ldg(&nrp->yscat0), ny = __ldg(&nrp->nyscat);
       const W invs = (W)__ldg(&nrp->invs);
       const W* pp = partials + (int64_t)(poff0 + ri.y) * R;
-      for (int c0 = 0; c0 < R; c0 += kMaxColsLane) {
+      {
+        const int c0 = (wu - it * ncb) * kMaxColsLane;
         const int nc = min(kMaxColsLane, R - c0);
         W acc[kMaxColsLane];
 #pragma unroll
@@ -875,7 +893,10 @@ cudaError_t launch_lc(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W*
 
 // Lane layout for nrhs columns: LC = the smallest power of two >= nrhs (at
 // most 32); two columns per lane for nrhs > 32 in fp32 when every row of X, B
-// and the scratch starts on an 8-byte boundary.
+// and the scratch starts on an 8-byte boundary; four columns per lane on
+// two lanes for 8 fp32 columns when they start on a 16-byte
+// boundary (fewer shared-memory loads per multiply-add in the leaf pass,
+// more lanes over the rows).
 template <typename W>
 cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* B, int64_t ldb, W* Y,
                      W* partials, unsigned long long* sync, unsigned long long base, cudaStream_t s,
@@ -885,6 +906,11 @@ cudaError_t launch_w(const HandleDev& hd, int nrhs, const W* X, int64_t ldx, W* 
   if (nrhs == 1) return HODLR_LAUNCH(1, 1);
   if (nrhs == 2) return HODLR_LAUNCH(2, 1);
   if (nrhs <= 4) return HODLR_LAUNCH(4, 1);
+  if constexpr (sizeof(W) == 4) {
+    const bool quads = nrhs <= 8 && nrhs % 4 == 0 && ldx % 4 == 0 && ldb % 4 == 0 && (uintptr_t)X % 16 == 0 &&
+                       (uintptr_t)B % 16 == 0;
+    if (quads) return HODLR_LAUNCH(2, 4);
+  }
   if (nrhs <= 8) return HODLR_LAUNCH(8, 1);
   if (nrhs <= 16) return HODLR_LAUNCH(16, 1);
   if constexpr (sizeof(W) == 4) {

@@ -178,6 +178,30 @@ def test_batches_and_strides_and_determinism():
     g.close()
 
 
+@pytest.mark.parametrize("ld,off", [(8, 0), (12, 4), (10, 1)])
+def test_eight_columns_lane_layouts(ld, off):
+    """Eight fp32 columns: four per lane when rows start on 16-byte
+    boundaries (contiguous X staged in shared memory, or strided X read
+    directly), one per lane otherwise (ldx = 10, odd offset)."""
+    n, depth, eps, work = 1500, 3, 1e-6, "fp32"
+    tiers = ("fp64", "fp32", "bf16", "fp16", "e4m3")
+    h = _oracle(n, depth, eps, SPEC_GAUSS, work, tiers)
+    g = _gpu(h, eps, work, tiers)
+    R = 8
+    Xfull = torch.from_numpy(synth.rhs_normal(n, ld, 21, np.float32)).cuda()
+    X = Xfull[:, off:off + R] if ld > R else Xfull
+    Bfull = torch.full((n, ld), 5.0, device="cuda")
+    Bv = Bfull[:, off:off + R] if ld > R else Bfull
+    g.matvec(X, out=Bv)
+    b = Bv.cpu().numpy().astype(np.float64)
+    X64 = X.cpu().numpy().astype(np.float64)
+    ref = M.hodlr_matvec(h, X64)
+    assert np.all(np.abs(b - ref) <= _tol(h, X64, ref, work))
+    if ld > R:
+        assert torch.all(Bfull[:, :off] == 5.0) and torch.all(Bfull[:, off + R:] == 5.0)
+    g.close()
+
+
 def test_single_generator_pair_on_gpu():
     """D = 0 and one generator pair: the GPU writes exactly U (V^T x_sib) on the
     rows of node i and zero elsewhere (level/sibling indexing)."""
