@@ -259,6 +259,28 @@ __device__ __forceinline__ float4 sld_v4f32(uint32_t a) {
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
 }
+__device__ __forceinline__ void sst_v4f32(uint32_t a, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+               : "memory");
+}
+// N consecutive values of W (16-byte aligned, N a multiple of 4)
+template <typename W, int N>
+__device__ __forceinline__ void sld_vec(uint32_t a, W (&v)[N]) {
+  if constexpr (sizeof(W) == 4) {
+#pragma unroll
+    for (int j4 = 0; j4 < N / 4; ++j4) {
+      const float4 t = sld_v4f32(a + 16u * j4);
+      v[4 * j4 + 0] = t.x;
+      v[4 * j4 + 1] = t.y;
+      v[4 * j4 + 2] = t.z;
+      v[4 * j4 + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int j2 = 0; j2 < N / 2; ++j2)
+      asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v[2 * j2]), "=d"(v[2 * j2 + 1]) : "r"(a + 16u * j2));
+  }
+}
 // one element of storage format P (compile time), decoded into W
 template <typename W, int P>
 __device__ __forceinline__ W sld_fmt(uint32_t a) {
@@ -715,10 +737,20 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
         // Y[:, c0 .. c0 + nc) of the leaf beside header and U, rows of
         // kMaxColsLane values (coalesced loads, one round trip)
         __syncwarp();
-        for (int e = lane; e < nq * kMaxColsLane; e += 32) {
-          const int q = e / kMaxColsLane, j = e - q * kMaxColsLane;
-          const W v = j < nc ? __ldcg(Yg + (int64_t)(yrow + q) * R + c0 + j) : (W)0;
-          sst<W>(ys_a + (uint32_t)(e * ebw), v);
+        if (sizeof(W) == 4 && nc == kMaxColsLane && R % 4 == 0) {
+          // four values per lane and load
+#pragma unroll 4
+          for (int e = lane; e < nq * (kMaxColsLane / 4); e += 32) {
+            const int q = e / (kMaxColsLane / 4), j4 = e - q * (kMaxColsLane / 4);
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(Yg + (int64_t)(yrow + q) * R + c0) + j4);
+            sst_v4f32(ys_a + (uint32_t)(e * 16), v);
+          }
+        } else {
+          for (int e = lane; e < nq * kMaxColsLane; e += 32) {
+            const int q = e / kMaxColsLane, j = e - q * kMaxColsLane;
+            const W v = j < nc ? __ldcg(Yg + (int64_t)(yrow + q) * R + c0 + j) : (W)0;
+            sst<W>(ys_a + (uint32_t)(e * ebw), v);
+          }
         }
         __syncwarp();
       }
@@ -776,10 +808,12 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
 #pragma unroll 2
             for (int c = 0; c < rU; ++c) {
               const W u = sld_fmt<W, TIER>(ucol + (uint32_t)(c * kTileRows * eb));
-              const uint32_t yq = ys_a + (uint32_t)((q + c) * kMaxColsLane * ebw);
+              // the staged Y row (zero past nc): vector loads, the same
+              // address for every lane
+              W yv[kMaxColsLane];
+              sld_vec<W, kMaxColsLane>(ys_a + (uint32_t)((q + c) * kMaxColsLane * ebw), yv);
 #pragma unroll
-              for (int j = 0; j < kMaxColsLane; ++j)
-                if (j < nc) uy[j] = fma(u, sld<W>(yq + (uint32_t)(j * ebw)), uy[j]);
+              for (int j = 0; j < kMaxColsLane; ++j) uy[j] = fma(u, yv[j], uy[j]);
             }
           } else {
             // too large for the slice: U and Y read directly
