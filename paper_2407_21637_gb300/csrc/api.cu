@@ -508,8 +508,22 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   // rows (one segment: a leaf or a piece of one), for every level, packed
   // up to kTcRows columns per group in level order.  The other chunks (and
   // every chunk in other working precisions) stay on the CUDA cores.
+  // The row table holds kTcRows entries per group, in group order: the
+  // byte offset of every A row's first element (-1: no row) and, in V
+  // groups, its partial row.
   const int n_tcg_leaf = (int)tcg.size();
   std::vector<TcVRow> tcv;
+  TcVRow no_row;
+  memset(&no_row, 0, sizeof(no_row));
+  no_row.off = -1;
+  no_row.prow = -1;
+  for (const TcGroup& gr : tcg) {
+    const size_t t0 = tcv.size();
+    tcv.resize(t0 + kTcRows, no_row);
+    const int lmp = (gr.m + 3) & ~3;
+    for (int r = 0; r < kTcRows; ++r)
+      if ((r >> 5) < gr.ntl) tcv[t0 + r].off = gr.doff[r >> 5] + (int64_t)(r & 31) * lmp * 4;
+  }
   h->vch_rest.clear();
   if (h->work == HODLR_FP32) {
     std::map<std::pair<int, int>, std::vector<int>> by_rows;   // (first row, rows) -> chunks
@@ -536,10 +550,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
           gr.vtab = (int)tcv.size();
           gr.xrow0 = kv.first.first;
           gr.m = kv.first.second;
-          TcVRow unused;
-          memset(&unused, 0, sizeof(unused));
-          unused.prow = -1;
-          tcv.resize(tcv.size() + kTcRows, unused);
+          tcv.resize(tcv.size() + kTcRows, no_row);
           open = true;
         }
         for (int a = 0; a < ch.rV; ++a) {
@@ -553,6 +564,47 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     }
   } else {
     h->vch_rest = h->vch;
+  }
+  // Tensor-core schedule: the groups are dealt to the CTAs of the launch
+  // (one per SM) longest first, each to the least loaded CTA, with a cost
+  // of (K chunks) x (1 + (32-row quarters of A) / 4) -- X conversion and
+  // MMAs per chunk, plus the A rows converted; each CTA's groups then sit
+  // together in the group array and the row table.
+  std::vector<int32_t> tc_first(1, 0);
+  if (!tcg.empty()) {
+    int dev = 0, sms = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int G = std::max(1, std::min<int>(sms, (int)tcg.size()));
+    std::vector<double> cost(tcg.size());
+    std::vector<int> order(tcg.size());
+    for (size_t g = 0; g < tcg.size(); ++g) {
+      cost[g] = ((tcg[g].m + 31) / 32) * (1.0 + ((tcg[g].rows + 31) / 32) / 4.0);
+      order[g] = (int)g;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> per(G);
+    std::vector<double> load(G, 0.0);
+    for (int g : order) {
+      const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      per[c].push_back(g);
+      load[c] += cost[g];
+    }
+    std::vector<TcGroup> tcg2;
+    std::vector<TcVRow> tcv2;
+    tcg2.reserve(tcg.size());
+    tcv2.reserve(tcv.size());
+    for (int c = 0; c < G; ++c) {
+      for (int g : per[c]) {
+        TcGroup gr = tcg[g];
+        if (gr.vtab >= 0) gr.vtab = (int)tcg2.size() * kTcRows;
+        tcv2.insert(tcv2.end(), tcv.begin() + (size_t)g * kTcRows, tcv.begin() + (size_t)(g + 1) * kTcRows);
+        tcg2.push_back(gr);
+      }
+      tc_first.push_back((int32_t)tcg2.size());
+    }
+    tcg.swap(tcg2);
+    tcv.swap(tcv2);
   }
 
   // ---- descriptors and scratch on the device ----
@@ -571,6 +623,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   if ((st = upload(ritems, &h->d_ritems)) != HODLR_OK) return st;
   if ((st = upload(tcg, &h->d_tcg)) != HODLR_OK) return st;
   if ((st = upload(tcv, &h->d_tcv)) != HODLR_OK) return st;
+  if ((st = upload(tc_first, &h->d_tc_first)) != HODLR_OK) return st;
   if ((st = upload(h->vch_rest, &h->d_vch_rest)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
   if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
@@ -604,6 +657,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   hd.tcg = h->d_tcg;
   hd.n_tcg = (int)tcg.size();
   hd.n_tcg_leaf = n_tcg_leaf;
+  hd.tc_first = h->d_tc_first;
+  hd.n_tc_cta = (int)tc_first.size() - 1;
   hd.tcv = h->d_tcv;
   hd.vch_rest = h->d_vch_rest;
   hd.n_vch_rest = (int)h->vch_rest.size();
@@ -761,7 +816,7 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
     cudaError_t e = cudaSuccess;
     if (tc && nb >= kTcMinCols) {
       if (ev) cudaEventRecord(ev[0], s);
-      e = launch_leaf_tc(h->hd.tcg, h->hd.n_tcg, h->hd.tcv, h->hd.pool, (const float*)(xb + c0 * es), ldx, nb,
+      e = launch_leaf_tc(h->hd.tcg, h->hd.tc_first, h->hd.n_tc_cta, h->hd.tcv, h->hd.pool, (const float*)(xb + c0 * es), ldx, nb,
                          (float*)(bb + c0 * es), ldb, (float*)h->d_partials, h->d_err, s);
       if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec leaf launch");
       if (ev) cudaEventRecord(ev[1], s);

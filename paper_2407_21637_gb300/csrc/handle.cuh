@@ -47,6 +47,7 @@ struct hodlr_s {
   int2* d_ritems = nullptr;
   TcGroup* d_tcg = nullptr;
   TcVRow* d_tcv = nullptr;
+  int32_t* d_tc_first = nullptr;
   VChunk* d_vch_rest = nullptr;
   P2Tile* d_p2 = nullptr;
   int32_t* d_yscat = nullptr;
@@ -71,6 +72,7 @@ struct hodlr_s {
     cudaFree(d_ritems);
     cudaFree(d_tcg);
     cudaFree(d_tcv);
+    cudaFree(d_tc_first);
     cudaFree(d_vch_rest);
     cudaFree(d_p2);
     cudaFree(d_yscat);

@@ -121,13 +121,14 @@ struct TcGroup {
   int32_t row0;                   // leaf group: first row of the group
   int32_t xrow0;                  // first row of X (K index 0)
   int32_t m;                      // K extent: leaf rows (leaf group) or valid chunk rows (V group)
-  int32_t vtab;                   // -1: leaf group; else first of its kTcRows entries in the row table
+  int32_t vtab;                   // -1: leaf group; V group g: g * kTcRows (its entries in the row table)
 };
-// One row of a V group: column c of a V chunk (K contiguous, fp32) and the
-// partial row it produces (-1: unused row).
+// One A row of a group (kTcRows per group, group g at entries g * kTcRows):
+// a row of a leaf block, or column c of a V chunk (K contiguous, fp32), and
+// in a V group the partial row it produces.
 struct TcVRow {
-  int64_t off;                    // byte offset in the pool of the column at the chunk's first row
-  int32_t prow;                   // partial row, or -1
+  int64_t off;                    // byte offset in the pool of the row's first element, or -1
+  int32_t prow;                   // V group: partial row, or -1
   int32_t pad_;
 };
 
@@ -145,14 +146,16 @@ struct HandleDev {
   const P2Tile* p2;
   const int32_t* yscat;
   const int2* ritems;             // reduction items: (NodeRed index, row of Y_node), all nodes
-  const TcGroup* tcg;             // tensor-core groups (leaf groups, then V groups)
+  const TcGroup* tcg;             // tensor-core groups, CTA c's at tc_first[c] .. tc_first[c + 1] - 1
+  const int32_t* tc_first;        // [n_tc_cta + 1]
   const TcVRow* tcv;              // row table of the V groups
   const VChunk* vch_rest;         // V chunks no V group covers (tensor-core mode)
   const uint8_t* pool;
   int* err;                       // device error word (bounded waits that gave up)
   int32_t n, depth, n_nodes, n_leaves;
   int32_t n_vch, n_nred, n_p2, n_ritems, n_tcg;
-  int32_t n_tcg_leaf;             // leaf groups (the first n_tcg_leaf of tcg)
+  int32_t n_tcg_leaf;             // leaf groups among them
+  int32_t n_tc_cta;               // CTAs of the tensor-core launch
   int32_t n_vch_rest;
   int32_t chunk_xrows_max;        // largest real-row span of a V chunk
   int32_t y_rows, p_rows;         // rows of the gathered Y and of the partial buffer
@@ -343,9 +346,11 @@ cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X
 // Tensor-core products (fp32 work, kTcMinCols <= nrhs <= kTcMaxCols):
 // B[rows of every leaf group] = D_i X[I_i]; for every V group, the partial
 // rows of its chunks = V_chunk^T X[I] (row-major, nrhs values per row).
-cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
-                           const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials,
-                           int* err, cudaStream_t s);
+// One CTA per entry of cta_first but the last; CTA c takes groups
+// cta_first[c] .. cta_first[c + 1] - 1.
+cudaError_t launch_leaf_tc(const TcGroup* groups, const int32_t* cta_first, int ncta, const TcVRow* vrows,
+                           const uint8_t* pool, const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb,
+                           float* partials, int* err, cudaStream_t s);
 // The grid size launch_matvec uses.
 int matvec_grid(const HandleDev& hd);
 // How far one launch advances the grid barrier counter (sync_base of the

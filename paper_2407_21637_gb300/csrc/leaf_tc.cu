@@ -199,7 +199,8 @@ __host__ __device__ inline uint32_t tc_smem_bytes(int N) {
 
 template <int N>
 __global__ void __launch_bounds__(kTcThreads, 1)
-leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __restrict__ vrows,
+leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ cta_first,
+               const TcVRow* __restrict__ vrows,
                const uint8_t* __restrict__ pool, const float* __restrict__ X, int64_t ldx, int R,
                float* __restrict__ B, int64_t ldb, float* __restrict__ partials, uint32_t tmem_cols, int* err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -240,9 +241,12 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
   constexpr uint32_t idesc = idesc_tf32(kTcM, 2 * N);   // B = [X_hi | X_lo]
   const bool x16 = (ldx % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
 
-  // this CTA's chunks, in order: (group, K-chunk)
+  // this CTA's chunks, in order: (group, K-chunk) (unrolled: the loads of
+  // several groups in flight together)
+  const int g0 = __ldg(cta_first + blockIdx.x), g1 = __ldg(cta_first + blockIdx.x + 1);   // this CTA's groups
   int total = 0;
-  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) total += (__ldg(&groups[g].m) + kKc - 1) / kKc;
+#pragma unroll 8
+  for (int g = g0; g < g1; ++g) total += (__ldg(&groups[g].m) + kKc - 1) / kKc;
 
   if (warp < kConvWarps) {
     const int t = threadIdx.x;
@@ -263,49 +267,32 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
     const int aq = warp & 3, akq = warp >> 2;
     const int arow = 32 * aq + lane;
     const uint32_t alane = (uint32_t)(32 * aq) << 16;
-    // load cursor state (per group)
-    int lg = blockIdx.x, lkc = 0;
-    const uint8_t* asrc[kAP];
-    bool aok[kAP];
-    int lm = 0, lmp = 0;
-    const float* xbase = X;
+    // load cursor state (per group).  load_group only issues the loads of
+    // a group's fields and row offsets; they are first used by the next
+    // chunk's copies, so their latency overlaps the conversion in between.
+    int lg = g0, lkc = 0;
+    int64_t aoff[kAP];   // byte offset of each A row's first element, -1: no row
+    int lm = 0, lxrow = 0;
     auto load_group = [&](int g) {
       const TcGroup* G = groups + g;
       lm = __ldg(&G->m);
-      lmp = (lm + 3) & ~3;
-      const int vt = __ldg(&G->vtab);
-      if (vt < 0) {
-        // leaf group: tile r / 32 holds rows r, row-major (stride lmp)
-        const int ntl = __ldg(&G->ntl);
+      lxrow = __ldg(&G->xrow0);
 #pragma unroll
-        for (int i = 0; i < kAP; ++i) {
-          const int r = rr + kAR * i;
-          aok[i] = (r >> 5) < ntl;
-          asrc[i] = aok[i] ? pool + __ldg(&G->doff[r >> 5]) + ((size_t)(r & 31) * lmp + 4 * cg) * 4 : pool;
-        }
-      } else {
-        // V group: row r is one V column, K contiguous
-#pragma unroll
-        for (int i = 0; i < kAP; ++i) {
-          const TcVRow* e = vrows + vt + rr + kAR * i;
-          aok[i] = __ldg(&e->prow) >= 0;
-          asrc[i] = aok[i] ? pool + __ldg(&e->off) + (size_t)cg * 16 : pool;
-        }
-      }
-      xbase = X + (int64_t)__ldg(&G->xrow0) * ldx;
+      for (int i = 0; i < kAP; ++i) aoff[i] = __ldg(&vrows[(size_t)g * kTcM + rr + kAR * i].off);
     };
-    if (lg < ngroups) load_group(lg);
+    if (lg < g1) load_group(lg);
     auto issue = [&](int u) {
       if (u < total) {
         const int k0 = lkc * kKc;
         const uint32_t ra = raw0 + (uint32_t)(u % kTcRaw) * rb, rx = ra + ab;
-        const bool kin = 4 * cg + k0 < lmp;
+        const bool kin = 4 * cg + k0 < ((lm + 3) & ~3);
 #pragma unroll
         for (int i = 0; i < kAP; ++i) {
-          const bool ok = aok[i] && kin;
-          cp_async16(ra + so0 + (uint32_t)(kAR * 128) * i, ok ? (const void*)(asrc[i] + (size_t)k0 * 4) : (const void*)pool,
-                     ok ? 16u : 0u);
+          const bool ok = aoff[i] >= 0 && kin;
+          cp_async16(ra + so0 + (uint32_t)(kAR * 128) * i,
+                     ok ? (const void*)(pool + aoff[i] + (size_t)(k0 + 4 * cg) * 4) : (const void*)pool, ok ? 16u : 0u);
         }
+        const float* xbase = X + (int64_t)lxrow * ldx;
 #pragma unroll
         for (int j = 0; j < XP; ++j) {
           const int p = t + kConvThreads * j;
@@ -328,8 +315,8 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
         }
         if (++lkc * kKc >= lm) {
           lkc = 0;
-          lg += gridDim.x;
-          if (lg < ngroups) load_group(lg);
+          ++lg;
+          if (lg < g1) load_group(lg);
         }
       }
       cp_async_commit();
@@ -337,9 +324,9 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
     // prologue: chunks 0 .. kTcRaw - 2 in flight
 #pragma unroll 1
     for (int u = 0; u < kTcRaw - 1; ++u) issue(u);
-    int cg_idx = blockIdx.x, ckc = 0;   // compute cursor
-    int cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
-    int crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
+    int cg_idx = g0, ckc = 0;   // compute cursor
+    int cm = cg_idx < g1 ? __ldg(&groups[cg_idx].m) : 0;
+    int crows = cg_idx < g1 ? __ldg(&groups[cg_idx].rows) : 0;
 #pragma unroll 1
     for (int u = 0; u < total; ++u) {
       const int r = u % kTcRaw, b = u & 1;
@@ -395,9 +382,9 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
       bar_arrive(&conv_done[b]);
       if (++ckc * kKc >= cm) {
         ckc = 0;
-        cg_idx += gridDim.x;
-        cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
-        crows = cg_idx < ngroups ? __ldg(&groups[cg_idx].rows) : 0;
+        ++cg_idx;
+        cm = cg_idx < g1 ? __ldg(&groups[cg_idx].m) : 0;
+        crows = cg_idx < g1 ? __ldg(&groups[cg_idx].rows) : 0;
       }
     }
     cp_async_wait<0>();
@@ -405,8 +392,8 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
     // ================= MMA issuer =================
     // group number gc accumulates into TMEM columns kTmemAcc (gc & 1); per
     // 8-wide K step, A_hi [X_hi | X_lo] + A_lo [X_hi | X_lo]
-    int ckc = 0, cg_idx = blockIdx.x, gc = 0;
-    int cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
+    int ckc = 0, cg_idx = g0, gc = 0;
+    int cm = cg_idx < g1 ? __ldg(&groups[cg_idx].m) : 0;
 #pragma unroll 1
     for (int u = 0; u < total; ++u) {
       const int b = u & 1;
@@ -438,8 +425,8 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
       __syncwarp();
       if (last) {
         ckc = 0;
-        cg_idx += gridDim.x;
-        cm = cg_idx < ngroups ? __ldg(&groups[cg_idx].m) : 0;
+        ++cg_idx;
+        cm = cg_idx < g1 ? __ldg(&groups[cg_idx].m) : 0;
         ++gc;
       } else {
         ++ckc;
@@ -452,7 +439,7 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
     const int row = 32 * q + lane;
     int gc = 0;
 #pragma unroll 1
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x, ++gc) {
+    for (int g = g0; g < g1; ++g, ++gc) {
       const TcGroup* G = groups + g;
       const bool okw = bar_wait(&acc_full[gc & 1], (uint32_t)((gc >> 1) & 1), err, 23) && !*(volatile int*)abort_flag;
       tc_fence_after();
@@ -502,23 +489,14 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, int ngroups, const TcVRow* __
   }
 }
 
-int tc_sms() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-  }
-  return n;
-}
-
 }  // namespace
 
 size_t leaf_tc_smem(int N) { return tc_smem_bytes(N); }
 
 namespace {
 template <int N>
-cudaError_t launch_n(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
+cudaError_t launch_n(const TcGroup* groups, const int32_t* cta_first, int ncta, const TcVRow* vrows,
+                     const uint8_t* pool,
                      const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials, int* err,
                      cudaStream_t s) {
   const uint32_t cols = kTmemCols;   // two accumulators, two A operand buffers
@@ -529,24 +507,24 @@ cudaError_t launch_n(const TcGroup* groups, int ngroups, const TcVRow* vrows, co
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
-  const int grid = std::min(ngroups, tc_sms());
-  leaf_tc_kernel<N><<<grid, kTcThreads, smem, s>>>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials,
+  leaf_tc_kernel<N><<<ncta, kTcThreads, smem, s>>>(groups, cta_first, vrows, pool, X, ldx, nrhs, B, ldb, partials,
                                                     cols, err);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_leaf_tc(const TcGroup* groups, int ngroups, const TcVRow* vrows, const uint8_t* pool,
+cudaError_t launch_leaf_tc(const TcGroup* groups, const int32_t* cta_first, int ncta, const TcVRow* vrows,
+                           const uint8_t* pool,
                            const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb, float* partials,
                            int* err, cudaStream_t s) {
-  if (ngroups == 0 || nrhs == 0) return cudaSuccess;
+  if (ncta == 0 || nrhs == 0) return cudaSuccess;
   const int N = (nrhs + 15) / 16 * 16;
   if (N < 16 || N > kTcMaxCols) return cudaErrorInvalidValue;
   switch (N) {
-    case 16: return launch_n<16>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
-    case 32: return launch_n<32>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
-    case 48: return launch_n<48>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
-    default: return launch_n<64>(groups, ngroups, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    case 16: return launch_n<16>(groups, cta_first, ncta, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    case 32: return launch_n<32>(groups, cta_first, ncta, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    case 48: return launch_n<48>(groups, cta_first, ncta, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
+    default: return launch_n<64>(groups, cta_first, ncta, vrows, pool, X, ldx, nrhs, B, ldb, partials, err, s);
   }
 }
 
