@@ -545,19 +545,33 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             const int srow0 = __ldg(&ch.seg[li].row0), sm = __ldg(&ch.seg[li].m), sprel = __ldg(&ch.seg[li].prel);
             const W* xgr = X + (int64_t)srow0 * ldx + kcol;
             const uint8_t* vrow = vbase + (int64_t)r0 * colbytes + (int64_t)sprel * eb;
-#pragma unroll 4
-            for (int pl = kl; pl < sm; pl += LK) {
-              W xv[CPL];
-              load_cols<W, CPL>(xgr + (int64_t)pl * ldx, true, xv);
-              const uint8_t* vp = vrow + (int64_t)pl * eb;
+            // UNR rows per lane at a time: every load of the block is issued
+            // before the first multiply-add (no branch between them: rows past
+            // the segment read its first row of the block with x = 0, columns
+            // past the rank read the last column and are never stored)
+            constexpr int UNR = (CPL >= 4 || sizeof(W) == 8) ? 2 : 4;
+            const int a_last = rV - 1 - r0;
+            for (int pl0 = kl; pl0 < sm; pl0 += UNR * LK) {
+              W xv[UNR][CPL];
+              W vv[UNR][RTA];
 #pragma unroll
-              for (int a = 0; a < RTA; ++a) {
-                if (r0 + a < rV) {
-                  const W v = gld_fmt<W, TIER>(vp + (int64_t)a * colbytes);
+              for (int u = 0; u < UNR; ++u) {
+                const int pl = pl0 + u * LK;
+                const bool rok = pl < sm;
+                const int pr = rok ? pl : pl0;
+                load_cols<W, CPL>(xgr + (int64_t)pr * ldx, true, xv[u]);
 #pragma unroll
-                  for (int j = 0; j < CPL; ++j) acc[a][j] = fma(v, xv[j], acc[a][j]);
-                }
+                for (int j = 0; j < CPL; ++j) xv[u][j] = rok ? xv[u][j] : (W)0;
+                const uint8_t* vp = vrow + (int64_t)pr * eb;
+#pragma unroll
+                for (int a = 0; a < RTA; ++a) vv[u][a] = gld_fmt<W, TIER>(vp + (int64_t)min(a, a_last) * colbytes);
               }
+#pragma unroll
+              for (int u = 0; u < UNR; ++u)
+#pragma unroll
+                for (int a = 0; a < RTA; ++a)
+#pragma unroll
+                  for (int j = 0; j < CPL; ++j) acc[a][j] = fma(vv[u][a], xv[u][j], acc[a][j]);
             }
           }
         };
