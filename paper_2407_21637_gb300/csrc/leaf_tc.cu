@@ -102,11 +102,12 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 __device__ __forceinline__ uint32_t sw128(int r, int g) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4));
 }
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
+// x rounded to tf32 (10 fraction bits) to nearest, ties away from zero, on
+// the bit pattern: half a unit of the 13 dropped bits is added to the
+// magnitude and the dropped bits are cleared (a carry into the exponent is
+// the rounding up to the next binade).  Two integer operations on the full-
+// rate pipes; finite x only.
+__device__ __forceinline__ uint32_t tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xffffe000u; }
 __device__ __forceinline__ void split(float x, uint32_t& hi, uint32_t& lo) {
   hi = tf32_rna(x);
   lo = tf32_rna(x - __uint_as_float(hi));
