@@ -223,17 +223,41 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
 hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
                                   void* B, int64_t ldb, int32_t xb_prec, void* stream);
 
+/* hodlr_sync_status -- wait for `stream`, then report whether a kernel of
+ * this handle gave up on a device-side wait since the last check.  Every
+ * wait in the library's kernels (a grid barrier, an mbarrier of a copy or of
+ * the tensor cores) is bounded: after two seconds the kernel records a code
+ * in the handle's device error word, finishes without further waiting and
+ * leaves the context usable; the results of that call are then undefined.
+ * Returns HODLR_ETIMEOUT (and clears the word; hodlr_last_error names the
+ * code) when a wait gave up, HODLR_OK otherwise; HODLR_ECUDA when the
+ * stream reports an error. */
+hodlr_status hodlr_sync_status(hodlr_t h, void* stream);
+
+/* hodlr_debug_stall_next -- test hook for the timeout path: the next
+ * hodlr_matvec call on this handle launches its first product kernel with
+ * grid-barrier targets that are never reached, so every CTA's barrier waits
+ * give up after their two-second limit (about four seconds in all) and
+ * hodlr_sync_status then returns HODLR_ETIMEOUT.  Nothing faults and no
+ * memory outside the call's own buffers is touched; later calls are
+ * unaffected. */
+hodlr_status hodlr_debug_stall_next(hodlr_t h);
+
 /* hodlr_profile -- enable (1) or disable (0) CUDA-event timing of the
  * kernels launched by the following hodlr_matvec calls on this handle (events
  * are recorded on the call's stream around each kernel of its last column
  * batch; recording costs a few microseconds of host time per call). */
 hodlr_status hodlr_profile(hodlr_t h, int32_t enable);
 
-/* hodlr_profile_read -- device time in ms of the last profiled hodlr_matvec
- * launch: ms[0] = the product kernel (all of Algorithm 3.3 in one persistent
- * launch), ms[1] = time after it up to the end of the call's work (0 when the
- * product is one launch).  count >= 2.  Waits for that call's events.
- * HODLR_EINVAL when profiling is off or nothing was profiled yet. */
+/* hodlr_profile_read -- device time in ms of the last column batch of the
+ * last profiled hodlr_matvec call.  On the CUDA cores alone (fewer than 16
+ * columns, or fp64 work): ms[0] = the product kernel (all of Algorithm 3.3 in
+ * one persistent launch), ms[1] = 0.  With the tensor cores (fp32 work, 16
+ * or more columns): ms[0] = the tensor-core kernel (leaf products D_i X and
+ * V_j^T X of the fp32 chunks), ms[1] = the product kernel that follows (the
+ * other chunks, the node reductions and U Y).  count >= 2.  Waits for that
+ * call's events.  HODLR_EINVAL when profiling is off or nothing was profiled
+ * yet. */
 hodlr_status hodlr_profile_read(hodlr_t h, float* ms, int32_t count);
 
 /* hodlr_info -- sizes, bytes per tier and the precision rule's quantities. */

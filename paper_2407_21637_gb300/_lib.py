@@ -66,6 +66,8 @@ SIGNATURES = {
     "hodlr_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                             ctypes.c_int32, _P]),
     "hodlr_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "hodlr_sync_status": (ctypes.c_int, [_P, _P]),
+    "hodlr_debug_stall_next": (ctypes.c_int, [_P]),
     "hodlr_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "hodlr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "hodlr_block_tiers": (ctypes.c_int, [_P, _I32P, _I32P]),

@@ -808,6 +808,10 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   // (batches of up to kTcMaxCols columns), low-rank part in the product
   // kernel; otherwise the product kernel alone (batches of h->batch)
   const bool tc = h->work == HODLR_FP32 && nrhs >= kTcMinCols && h->hd.n_tcg_leaf > 0;
+  // hodlr_debug_stall_next: the first launch of this call waits for grid
+  // barrier arrivals that never come (the counter itself advances as usual)
+  unsigned long long skew = h->stall_next ? 4ull * matvec_sync_step(h->hd) : 0ull;
+  h->stall_next = false;
   const int step = tc ? std::min(h->max_nrhs, kTcMaxCols) : h->batch;
   for (int c0 = 0; c0 < nrhs; c0 += step) {
     const int nb = std::min(step, nrhs - c0);
@@ -821,14 +825,16 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
       if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec leaf launch");
       if (ev) cudaEventRecord(ev[1], s);
       e = launch_matvec(h->hd, h->work, nb, xb + c0 * es, ldx, bb + c0 * es, ldb, h->d_Y, h->d_partials,
-                        h->d_sync, h->sync_base, s, nullptr, 1);
+                        h->d_sync, h->sync_base + skew, s, nullptr, 1);
+      skew = 0;
       if (ev) cudaEventRecord(ev[2], s);
     } else {
       for (int d0 = 0; d0 < nb && e == cudaSuccess; d0 += h->batch) {
         const int nd = std::min(h->batch, nb - d0);
         const bool lastd = d0 + h->batch >= nb;
         e = launch_matvec(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_Y,
-                          h->d_partials, h->d_sync, h->sync_base, s, lastd ? ev : nullptr);
+                          h->d_partials, h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
+        skew = 0;
         if (!lastd) h->sync_base += matvec_sync_step(h->hd);
       }
     }
@@ -836,6 +842,22 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
   }
   if (h->prof_on) h->prof_valid = true;
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_sync_status(hodlr_t h, void* stream) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int code = 0;
+  CK(cudaMemcpy(&code, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code == 0) return HODLR_OK;
+  CK(cudaMemset(h->d_err, 0, sizeof(int)));
+  return fail(HODLR_ETIMEOUT, "a device wait gave up (code " + std::to_string(code) + ")");
+}
+
+hodlr_status hodlr_debug_stall_next(hodlr_t h) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  h->stall_next = true;
   return HODLR_OK;
 }
 

@@ -56,6 +56,7 @@ struct hodlr_s {
   void* d_partials = nullptr;
   unsigned long long* d_sync = nullptr;   // grid barrier counter of the product kernel
   unsigned long long sync_base = 0;       // its value before the next launch
+  bool stall_next = false;                // hodlr_debug_stall_next: next product's barrier unreachable
   size_t scratch_bytes = 0;
   HandleDev hd{};
   cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};

@@ -135,6 +135,16 @@ class HodlrMatrix:
                                   _stream_ptr(stream)), "hodlr_matvec")
         return out.view(-1) if vec and out.dim() == 2 else out
 
+    def sync_status(self, stream=None):
+        """hodlr_sync_status: wait for the stream; raise HodlrError
+        (HODLR_ETIMEOUT) when a device-side wait of this handle gave up."""
+        check(load().hodlr_sync_status(self._h, _stream_ptr(stream)), "hodlr_sync_status")
+
+    def debug_stall_next(self):
+        """hodlr_debug_stall_next: the next matvec's grid barrier waits run
+        out (a test of the timeout path)."""
+        check(load().hodlr_debug_stall_next(self._h), "hodlr_debug_stall_next")
+
     # ---- inspection ---------------------------------------------------
     def info(self) -> dict:
         inf = Info()

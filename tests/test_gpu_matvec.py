@@ -68,10 +68,11 @@ def _tol(h, X, ref, work):
     stored factors: Higham's standard model for the longest accumulation
     chain N (gamma_N(u) g + 2u g for the format decode and scaling, u |b| for
     the final rounding), g = |U|(|V|^T |x|) + |D||x|.  With TC_MIN_COLS or more
-    fp32 columns the leaf products run on the tensor cores as three tf32
-    products (hi*hi + hi*lo + lo*hi); each product then carries up to about
-    3 * 2^-22 = 12u relative error and the fp32 accumulation of the tensor
-    core is allowed 2u per addition: (gamma_N(2u) + 12u) g + u |b|."""
+    fp32 columns the leaf products and V^T X of the fp32 chunks run on the
+    tensor cores on the tf32 hi/lo split of both factors; each product then
+    carries up to about 2 * 2^-22 = 8u relative error (14u allowed) and the
+    fp32 accumulation of the tensor core is allowed 2u per addition:
+    (gamma_N(2u) + 14u) g + u |b|."""
     u = F.unit_roundoff(work)
     g = M.abs_product(h, X)
     if work == "fp32" and X.shape[1] >= TC_MIN_COLS:
