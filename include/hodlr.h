@@ -223,6 +223,22 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
 hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
                                   void* B, int64_t ldb, int32_t xb_prec, void* stream);
 
+/* hodlr_save -- write the stored matrix to `path`: sizes and options, every
+ * block's rank, format and power-of-two scales, the hodlr_info_t summary and
+ * the stored generators and leaves decoded to fp64 (exact).  Host byte order;
+ * the file is meant for the same library on the same kind of host.  Waits
+ * for `stream`.  Errors: HODLR_EINVAL (null arguments, file not writable),
+ * HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_save(hodlr_t h, const char* path, void* stream);
+
+/* hodlr_load -- a new handle from a hodlr_save file, stored exactly as the
+ * saved one (the same formats and scales, bitwise the same stored values, so
+ * bitwise the same products; the precision rule is not applied again).  The
+ * file is checked (magic, version, sizes, formats) before any device work.
+ * Waits for `stream`.  Errors: HODLR_EINVAL (unreadable, truncated or corrupt
+ * file), HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_load(const char* path, void* stream, hodlr_t* out);
+
 /* hodlr_sync_status -- wait for `stream`, then report whether a kernel of
  * this handle gave up on a device-side wait since the last check.  Every
  * wait in the library's kernels (a grid barrier, an mbarrier of a copy or of

@@ -66,6 +66,8 @@ SIGNATURES = {
     "hodlr_matvec_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                             ctypes.c_int32, _P]),
     "hodlr_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "hodlr_save": (ctypes.c_int, [_P, ctypes.c_char_p, _P]),
+    "hodlr_load": (ctypes.c_int, [ctypes.c_char_p, _P, ctypes.POINTER(_P)]),
     "hodlr_sync_status": (ctypes.c_int, [_P, _P]),
     "hodlr_debug_stall_next": (ctypes.c_int, [_P]),
     "hodlr_profile": (ctypes.c_int, [_P, ctypes.c_int32]),

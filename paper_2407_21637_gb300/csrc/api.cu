@@ -261,6 +261,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     }
   }
 
+  if (!h->force_tier.empty()) block_tier = h->force_tier;   // hodlr_load
+
   // ---- formats and scales of every generator ----
   const int ebw = prec_bytes(h->work);
   std::vector<double> sU(nnodes, 1.0), sV(nnodes, 1.0);
@@ -270,8 +272,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       NodeDev& nd = h->nodes[q];
       nd.tierU = block_tier[q];
       nd.tierV = block_tier[node_index(k, i ^ 1)];
-      sU[q] = pow2_scale(amax[nnodes + q], nd.tierU);
-      sV[q] = pow2_scale(amax[q], nd.tierV);
+      sU[q] = h->force_sU.empty() ? pow2_scale(amax[nnodes + q], nd.tierU) : h->force_sU[q];
+      sV[q] = h->force_sV.empty() ? pow2_scale(amax[q], nd.tierV) : h->force_sV[q];
       nd.invsU = 1.0 / sU[q];
       nd.invsV = 1.0 / sV[q];
       inf.max_rank = std::max(inf.max_rank, nd.rU);
@@ -787,6 +789,147 @@ hodlr_status hodlr_export(hodlr_t h, double* const* U, double* const* V, double*
   for (size_t l = 0; l < h->leaves.size(); ++l)
     if (D && D[l])
       memcpy(D[l], &host[h->st_D[l]], sizeof(double) * h->leaves[l].m * h->leaves[l].m);
+  return HODLR_OK;
+}
+
+// ---- hodlr_save / hodlr_load ----------------------------------------------
+// File: SaveHeader, then per node (2^(depth+1) - 2 of them) the rank, the
+// block format and the power-of-two scales of U and V, then hodlr_info_t,
+// then the stored generators and leaves decoded to fp64 (the export staging
+// layout, st_count values).  Host byte order.
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int32_t version, n, depth, work, per_block, max_nrhs;
+  uint32_t avail;
+  int32_t pad_;
+  double eps;
+  int64_t st_count;
+};
+constexpr char kSaveMagic[8] = {'H', 'O', 'D', 'L', 'R', 'S', 'V', '1'};
+
+struct File {
+  FILE* f = nullptr;
+  ~File() { if (f) fclose(f); }
+};
+}  // namespace
+
+hodlr_status hodlr_save(hodlr_t h, const char* path, void* stream) {
+  g_last_error.clear();
+  if (!h || !path) return fail(HODLR_EINVAL, "null handle/path");
+  const int nnodes = (int)h->nodes.size(), nleaves = (int)h->leaves.size();
+  std::vector<double> host;
+  try { host.resize((size_t)h->st_count); } catch (...) { return fail(HODLR_ENOMEM, "host staging"); }
+  {
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf d_stage, d_tasks;
+    if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(h->st_count, 1)) != cudaSuccess)
+      return fail(HODLR_ENOMEM, "save staging");
+    CK(cudaMalloc(&d_tasks.p, std::max<size_t>(h->tasks.size(), 1) * sizeof(PackTask)));
+    CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask), cudaMemcpyHostToDevice, s));
+    CK(launch_unpack(h->d_pool, (const PackTask*)d_tasks.p, (int)h->tasks.size(), (double*)d_stage.p, s));
+    CK(cudaMemcpyAsync(host.data(), d_stage.p, sizeof(double) * h->st_count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  SaveHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kSaveMagic, 8);
+  hd.version = 1;
+  hd.n = h->n;
+  hd.depth = h->depth;
+  hd.work = h->work;
+  hd.per_block = h->per_block;
+  hd.max_nrhs = h->max_nrhs;
+  hd.avail = h->avail;
+  hd.eps = h->eps;
+  hd.st_count = h->st_count;
+  std::vector<int32_t> rank(nnodes), tier(nnodes);
+  std::vector<double> sU(nnodes), sV(nnodes);
+  for (int q = 0; q < nnodes; ++q) {
+    rank[q] = h->nodes[q].rU;
+    tier[q] = h->nodes[q].tierU;
+    sU[q] = 1.0 / h->nodes[q].invsU;
+    sV[q] = 1.0 / h->nodes[q].invsV;
+  }
+  (void)nleaves;
+  File fl;
+  fl.f = fopen(path, "wb");
+  if (!fl.f) return fail(HODLR_EINVAL, std::string("cannot open for writing: ") + path);
+  bool ok = fwrite(&hd, sizeof(hd), 1, fl.f) == 1;
+  if (nnodes) {
+    ok = ok && fwrite(rank.data(), sizeof(int32_t), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fwrite(tier.data(), sizeof(int32_t), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fwrite(sU.data(), sizeof(double), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fwrite(sV.data(), sizeof(double), nnodes, fl.f) == (size_t)nnodes;
+  }
+  ok = ok && fwrite(&h->info, sizeof(hodlr_info_t), 1, fl.f) == 1;
+  ok = ok && fwrite(host.data(), sizeof(double), host.size(), fl.f) == host.size();
+  ok = (fclose(fl.f) == 0) && ok;
+  fl.f = nullptr;
+  if (!ok) return fail(HODLR_EINVAL, std::string("write failed: ") + path);
+  return HODLR_OK;
+}
+
+hodlr_status hodlr_load(const char* path, void* stream, hodlr_t* out) {
+  g_last_error.clear();
+  if (!path || !out) return fail(HODLR_EINVAL, "null path/out");
+  File fl;
+  fl.f = fopen(path, "rb");
+  if (!fl.f) return fail(HODLR_EINVAL, std::string("cannot open: ") + path);
+  SaveHeader hd;
+  if (fread(&hd, sizeof(hd), 1, fl.f) != 1 || memcmp(hd.magic, kSaveMagic, 8) != 0 || hd.version != 1)
+    return fail(HODLR_EINVAL, "not a hodlr_save file (magic/version)");
+  if (hd.depth < 0 || hd.depth > HODLR_MAX_DEPTH || hd.n < 1 || ((int64_t)1 << hd.depth) > hd.n || hd.st_count < 0)
+    return fail(HODLR_EINVAL, "corrupt hodlr_save header");
+  const int nnodes = (1 << (hd.depth + 1)) - 2;
+  std::vector<int32_t> rank(nnodes), tier(nnodes);
+  std::vector<double> sU(nnodes), sV(nnodes);
+  bool ok = true;
+  if (nnodes) {
+    ok = fread(rank.data(), sizeof(int32_t), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fread(tier.data(), sizeof(int32_t), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fread(sU.data(), sizeof(double), nnodes, fl.f) == (size_t)nnodes;
+    ok = ok && fread(sV.data(), sizeof(double), nnodes, fl.f) == (size_t)nnodes;
+  }
+  hodlr_info_t info;
+  ok = ok && fread(&info, sizeof(info), 1, fl.f) == 1;
+  if (!ok) return fail(HODLR_EINVAL, "truncated hodlr_save file");
+  for (int q = 0; q < nnodes; ++q)
+    if (tier[q] < 0 || tier[q] >= kPrecCount || !((hd.avail >> tier[q]) & 1u) || !(sU[q] > 0.0) || !(sV[q] > 0.0))
+      return fail(HODLR_EINVAL, "corrupt hodlr_save file (formats/scales)");
+  hodlr_opts opts;
+  memset(&opts, 0, sizeof(opts));
+  opts.eps = hd.eps;
+  opts.work = hd.work;
+  opts.tier_mask = hd.avail;
+  opts.per_block = hd.per_block;
+  opts.max_nrhs = hd.max_nrhs;
+  auto h = new hodlr_s();
+  std::unique_ptr<hodlr_s> guard(h);
+  hodlr_status st = plan_layout(h, hd.n, hd.depth, rank.data(), &opts);
+  if (st != HODLR_OK) return st;
+  if (h->st_count != hd.st_count) return fail(HODLR_EINVAL, "corrupt hodlr_save file (sizes)");
+  std::vector<double> host;
+  try { host.resize((size_t)h->st_count); } catch (...) { return fail(HODLR_ENOMEM, "host staging"); }
+  if (fread(host.data(), sizeof(double), host.size(), fl.f) != host.size())
+    return fail(HODLR_EINVAL, "truncated hodlr_save file (values)");
+  h->force_tier.assign(tier.begin(), tier.end());
+  h->force_sU = sU;
+  h->force_sV = sV;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf d_stage;
+  if (cudaMalloc(&d_stage.p, sizeof(double) * std::max<int64_t>(h->st_count, 1)) != cudaSuccess)
+    return fail(HODLR_ENOMEM, "device staging");
+  CK(cudaMemcpyAsync(d_stage.p, host.data(), sizeof(double) * h->st_count, cudaMemcpyHostToDevice, s));
+  st = finish_from_staging(h, (const double*)d_stage.p, nullptr, nullptr, &opts, s);
+  if (st != HODLR_OK) return st;
+  h->force_tier.clear();
+  h->force_sU.clear();
+  h->force_sV.clear();
+  const int64_t device_bytes = h->info.device_bytes;
+  h->info = info;
+  h->info.device_bytes = device_bytes;
+  *out = guard.release();
   return HODLR_OK;
 }
 

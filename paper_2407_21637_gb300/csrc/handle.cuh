@@ -57,6 +57,10 @@ struct hodlr_s {
   unsigned long long* d_sync = nullptr;   // grid barrier counter of the product kernel
   unsigned long long sync_base = 0;       // its value before the next launch
   bool stall_next = false;                // hodlr_debug_stall_next: next product's barrier unreachable
+  // hodlr_load: formats and power-of-two scales restored from a file instead
+  // of chosen by the precision rule (empty otherwise)
+  std::vector<int> force_tier;
+  std::vector<double> force_sU, force_sV;
   size_t scratch_bytes = 0;
   HandleDev hd{};
   cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};

@@ -135,6 +135,20 @@ class HodlrMatrix:
                                   _stream_ptr(stream)), "hodlr_matvec")
         return out.view(-1) if vec and out.dim() == 2 else out
 
+    def save(self, path: str, stream=None):
+        """hodlr_save: write the stored matrix (exactly) to a file."""
+        check(load().hodlr_save(self._h, str(path).encode(), _stream_ptr(stream)), "hodlr_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "HodlrMatrix":
+        """hodlr_load: a handle stored exactly as the saved one."""
+        lib = load()
+        h = ctypes.c_void_p()
+        check(lib.hodlr_load(str(path).encode(), _stream_ptr(stream), ctypes.byref(h)), "hodlr_load")
+        inf = Info()
+        check(lib.hodlr_info(h, ctypes.byref(inf)), "hodlr_info")
+        return cls(h, inf.n, inf.depth, PREC_NAME[inf.work])
+
     def sync_status(self, stream=None):
         """hodlr_sync_status: wait for the stream; raise HodlrError
         (HODLR_ETIMEOUT) when a device-side wait of this handle gave up."""
@@ -168,7 +182,8 @@ class HodlrMatrix:
         check(load().hodlr_profile(self._h, int(enable)), "hodlr_profile")
 
     def profile_read(self):
-        """hodlr_profile_read: (phase-1 ms, phase-2 ms) of the last profiled product."""
+        """hodlr_profile_read: device ms of the two kernels of the last profiled
+        product (tensor-core kernel, product kernel), or (product kernel, 0)."""
         ms = (ctypes.c_float * 2)()
         check(load().hodlr_profile_read(self._h, ms, 2), "hodlr_profile_read")
         return float(ms[0]), float(ms[1])

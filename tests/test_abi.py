@@ -70,3 +70,16 @@ def test_validation_before_device_work(lib):
                                          ctypes.c_void_p(8), 1, ctypes.c_void_p(8), 1, None) == 1
     assert h.value is None
     lib.hodlr_destroy(None)
+
+
+def test_load_rejects_bad_files_before_device_work(lib, tmp_path):
+    h = ctypes.c_void_p()
+    assert lib.hodlr_load(str(tmp_path / "missing.hodlr").encode(), None, ctypes.byref(h)) == 1
+    bad = tmp_path / "bad.hodlr"
+    bad.write_bytes(b"NOTHODLR" + bytes(64))
+    assert lib.hodlr_load(str(bad).encode(), None, ctypes.byref(h)) == 1
+    assert b"magic" in lib.hodlr_last_error()
+    short = tmp_path / "short.hodlr"
+    short.write_bytes(b"HODLRSV1" + bytes(8))
+    assert lib.hodlr_load(str(short).encode(), None, ctypes.byref(h)) == 1
+    assert not h.value
