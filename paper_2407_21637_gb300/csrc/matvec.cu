@@ -46,6 +46,9 @@ constexpr int kRedWarps = 3;                  // node-reduction warps
 constexpr int kP2Threads = kCThreads + 32 + 32 * kRedWarps;   // consumers, producer, reducers
 constexpr int kMaxStages = 6;
 constexpr int kMaxColsLane = 16;              // right-hand sides per lane and step of pass 2
+constexpr int kP1Rows = 4;                    // pass 1: tile rows per consumer warp
+constexpr int kP1Warps = 8;                   // pass 1: warps per tile (kP1Rows * kP1Warps = 32 rows)
+constexpr int kP1Groups = 2;                  // pass 1: tiles in work at once per CTA
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // every wait gives up after 2 s
 
 template <typename W> struct WorkPrec;
@@ -371,7 +374,7 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   if (threadIdx.x == 0) {
     for (int s = 0; s < nstages; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kCWarps);
+      mbar_init(&empty[s], kP1Warps);
     }
     for (int w = 0; w < kCWarps; ++w) mbar_init(&wbarA[w], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -607,12 +610,16 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     asm volatile("bar.sync 3, %0;" ::"r"(kRedBar) : "memory");
   }
 
-  // ---- pass 1: D[rows, :] X[I_i] for every tile; warp w owns rows 2w, 2w + 1 ----
-  static_assert(kTileRows == 2 * kCWarps, "two rows per consumer warp");
+  // ---- pass 1: D[rows, :] X[I_i] for every tile.  The consumers work in
+  //      kP1Groups groups of kP1Warps warps; group g takes tiles g, g +
+  //      kP1Groups, ... and warp w of a group owns rows kP1Rows w ..
+  //      kP1Rows w + kP1Rows - 1 of the tile (each X value read from shared
+  //      memory serves kP1Rows rows) ----
+  static_assert(kP1Rows * kP1Warps == kTileRows && kP1Warps * kP1Groups == kCWarps, "pass-1 warp layout");
   static_assert(kTileRows == 32, "one lane per tile row in pass 2");
   {
-    const int ra = 2 * warp, rb = 2 * warp + 1;
-    for (int tl = 0; tl < (skip_leaf ? 0 : ntiles); ++tl) {
+    const int grp = warp / kP1Warps, r0w = kP1Rows * (warp - grp * kP1Warps);
+    for (int tl = grp; tl < (skip_leaf ? 0 : ntiles); tl += kP1Groups) {
       const int s = tl % nstages;
       if (!mbar_wait(&full[s], (tl / nstages) & 1, hd.err, 4)) {
         alive = false;
@@ -624,14 +631,16 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
       // pass-1 results of tile tl, column by column (32 rows per column)
       const uint32_t res_t = smem_u32(res) + (uint32_t)((size_t)tl * kTileRows * R * ebw);
       const int mp = (t.m + 3) & ~3;   // D row length
-      const uint32_t da = st_a + (uint32_t)(ra * mp * ebw), db = da + (uint32_t)(mp * ebw);
+      const uint32_t da = st_a + (uint32_t)(r0w * mp * ebw), drs = (uint32_t)(mp * ebw);
       for (int c0 = 0; c0 < R; c0 += BW) {
         const int col = c0 + cl * CPL;
         const bool cok = col < R;
         const int kcol = cok ? col : 0;   // lanes past the last column read column 0 and drop it
-        W acc0[CPL], acc1[CPL];
+        W acc[kP1Rows][CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) acc0[j] = acc1[j] = (W)0;
+        for (int i = 0; i < kP1Rows; ++i)
+#pragma unroll
+          for (int j = 0; j < CPL; ++j) acc[i][j] = (W)0;
         bool done = false;
         if constexpr (LC == 1 && CPL == 1 && sizeof(W) == 4) {
           if (xstage_bytes) {
@@ -639,16 +648,14 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             // consecutive columns of D per lane and step
             for (int k = 4 * lane; k < t.m; k += 128) {
               const float4 x4 = sld_v4f32(xs_a + (uint32_t)(k * 4));
-              const float4 a4 = sld_v4f32(da + (uint32_t)(k * 4));
-              const float4 b4 = sld_v4f32(db + (uint32_t)(k * 4));
-              acc0[0] = fmaf(a4.x, x4.x, acc0[0]);
-              acc1[0] = fmaf(b4.x, x4.x, acc1[0]);
-              acc0[0] = fmaf(a4.y, x4.y, acc0[0]);
-              acc1[0] = fmaf(b4.y, x4.y, acc1[0]);
-              acc0[0] = fmaf(a4.z, x4.z, acc0[0]);
-              acc1[0] = fmaf(b4.z, x4.z, acc1[0]);
-              acc0[0] = fmaf(a4.w, x4.w, acc0[0]);
-              acc1[0] = fmaf(b4.w, x4.w, acc1[0]);
+#pragma unroll
+              for (int i = 0; i < kP1Rows; ++i) {
+                const float4 a4 = sld_v4f32(da + i * drs + (uint32_t)(k * 4));
+                acc[i][0] = fmaf(a4.x, x4.x, acc[i][0]);
+                acc[i][0] = fmaf(a4.y, x4.y, acc[i][0]);
+                acc[i][0] = fmaf(a4.z, x4.z, acc[i][0]);
+                acc[i][0] = fmaf(a4.w, x4.w, acc[i][0]);
+              }
             }
             done = true;
           }
@@ -659,11 +666,11 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             for (int k = kl; k < t.m; k += LK) {
               W xv[CPL];
               sld_cols<W, CPL>(xs_a + (uint32_t)((k * R + kcol) * ebw), xv);
-              const W d0 = sld<W>(da + (uint32_t)(k * ebw)), d1 = sld<W>(db + (uint32_t)(k * ebw));
 #pragma unroll
-              for (int j = 0; j < CPL; ++j) {
-                acc0[j] = fma(d0, xv[j], acc0[j]);
-                acc1[j] = fma(d1, xv[j], acc1[j]);
+              for (int i = 0; i < kP1Rows; ++i) {
+                const W d = sld<W>(da + i * drs + (uint32_t)(k * ebw));
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) acc[i][j] = fma(d, xv[j], acc[i][j]);
               }
             }
           } else {
@@ -672,33 +679,32 @@ matvec_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             for (int k = kl; k < t.m; k += LK) {
               W xv[CPL];
               load_cols<W, CPL>(xg + (int64_t)k * ldx, true, xv);
-              const W d0 = sld<W>(da + (uint32_t)(k * ebw)), d1 = sld<W>(db + (uint32_t)(k * ebw));
 #pragma unroll
-              for (int j = 0; j < CPL; ++j) {
-                acc0[j] = fma(d0, xv[j], acc0[j]);
-                acc1[j] = fma(d1, xv[j], acc1[j]);
+              for (int i = 0; i < kP1Rows; ++i) {
+                const W d = sld<W>(da + i * drs + (uint32_t)(k * ebw));
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) acc[i][j] = fma(d, xv[j], acc[i][j]);
               }
             }
           }
         }
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
+        for (int i = 0; i < kP1Rows; ++i)
 #pragma unroll
-          for (int o = LC; o < 32; o <<= 1) {
-            acc0[j] += __shfl_xor_sync(0xffffffffu, acc0[j], o);
-            acc1[j] += __shfl_xor_sync(0xffffffffu, acc1[j], o);
+          for (int j = 0; j < CPL; ++j) {
+#pragma unroll
+            for (int o = LC; o < 32; o <<= 1) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], o);
           }
-        }
         if (kl == 0 && cok) {
-          if (res_smem) {
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-              sst<W>(res_t + (uint32_t)(((col + j) * kTileRows + ra) * ebw), acc0[j]);
-              sst<W>(res_t + (uint32_t)(((col + j) * kTileRows + rb) * ebw), acc1[j]);
+          for (int i = 0; i < kP1Rows; ++i) {
+            const int ra = r0w + i;
+            if (res_smem) {
+#pragma unroll
+              for (int j = 0; j < CPL; ++j) sst<W>(res_t + (uint32_t)(((col + j) * kTileRows + ra) * ebw), acc[i][j]);
+            } else if (ra < t.rows) {
+              store_cols<W, CPL>(B + (int64_t)(t.row0 + ra) * ldb + col, acc[i]);
             }
-          } else {
-            if (ra < t.rows) store_cols<W, CPL>(B + (int64_t)(t.row0 + ra) * ldb + col, acc0);
-            if (rb < t.rows) store_cols<W, CPL>(B + (int64_t)(t.row0 + rb) * ldb + col, acc1);
           }
         }
       }
