@@ -55,6 +55,27 @@ SIMT_COLS = 16        # columns per launch of the CUDA-core product kernel at mo
 MAX_NRHS = 64         # the handle's max_nrhs in this benchmark
 
 
+# DRAM bytes (read + written) per step of each product kernel, summed over
+# the step's launches of the kernel, from one ncu capture of this benchmark
+# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
+# library's CUDA sources are the ones they were measured on (their SHA-256),
+# else null.
+TRAFFIC_SRC_SHA = None
+TRAFFIC_PER_STEP = {}
+
+
+def _csrc_sha():
+    import hashlib
+    d = os.path.join(ROOT, "paper_2407_21637_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
 def _launches(R):
     """Kernel launches of one product with R columns (the library's batching)."""
     if WL["work"] == "fp32" and R >= TC_MIN_COLS:
@@ -395,9 +416,12 @@ def run_ours(args, rank, world, dist):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dominant,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": peak_kind,
-                     "bytes_per_launch": "algorithmic bytes of each launch of the kernel (see DESIGN.md), "
-                                         "summed over the step's launches and divided by their summed time",
+                     "traffic": (TRAFFIC_PER_STEP.get(dominant) if TRAFFIC_SRC_SHA == _csrc_sha() else None),
+                     "traffic_per": "step (the kernel's launches of one step, like achieved)",
+                     "peak_source": peak_kind,
+                     "bytes_per_launch": "algorithmic bytes of each launch of the kernel (factors, leaves, "
+                                         "X read once, B written once), summed over the step's launches "
+                                         "and divided by their summed time",
                      "kernels": {k: {"bytes": v[0], "us": v[1] * 1e3,
                                      "GBps": (v[0] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
                                  for k, v in kernels.items()}},
