@@ -76,6 +76,21 @@ def _csrc_sha():
     return h.hexdigest()
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_rank, world, ms_step):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_rank / (ms_step * 1e-3)
+
+
 def _launches(R):
     """Kernel launches of one product with R columns (the library's batching)."""
     if WL["work"] == "fp32" and R >= TC_MIN_COLS:
@@ -295,13 +310,9 @@ def run_ours(args, rank, world, dist):
     per_R = {R: [] for R in rhs}
     for (R, e0, e1) in log:
         per_R[R].append(e0.elapsed_time(e1))
-    ms_step = float(sum(np.mean(per_R[R]) for R in rhs))
-    if dist is not None:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(sum(np.mean(per_R[R]) for R in rhs)), dist, dev)
     units_rank = sum(rhs) * n
-    value = world * units_rank / (ms_step * 1e-3)
+    value = job_value(units_rank, world, ms_step)
 
     # ---- per-kernel profile (separate untimed pass, same flush discipline) ----
     g.profile(True)
@@ -362,11 +373,7 @@ def run_ours(args, rank, world, dist):
             tot += e0.elapsed_time(e1)
         if it >= args.warmup:
             e2e_ms.append(tot)
-    e2e_step = float(np.mean(e2e_ms))
-    if dist is not None:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(float(np.mean(e2e_ms)), dist, dev)
     io_bytes = sum(n * R * es for R in rhs)
 
     # ---- backward errors against the dense kernel matrix, FP64 HODLR at equal eps ----
@@ -430,7 +437,7 @@ def run_ours(args, rank, world, dist):
                     "bytes_per_tier": info["bytes_per_tier"], "max_rank": info["max_rank"],
                     "level_tier": info["level_tier"][1:], "u_prime": info["u_prime"][1:],
                     "build_s": t_build},
-        "e2e": {"value": world * units_rank / (e2e_step * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_value(units_rank, world, e2e_step), "unit": UNIT,
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                 "ms_per_step": e2e_step},
         "gpu_launches": args.steps * sum(_launches(R) for R in rhs),
