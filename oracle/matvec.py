@@ -74,6 +74,48 @@ def hodlr_matvec(h, X, work: str = "fp64", stored: bool = True) -> np.ndarray:
     return B[:, 0] if vec else B
 
 
+def _rows_product(h, X, rows, stored, absval):
+    """Rows ``rows`` of the two-stage product of Algorithm 3.3 in fp64 (or of
+    its absolute-value twin g): for an output row r in node i of level k,
+    U_i[r] (V_{i^1}^T x_{i^1}) summed over the levels, plus D_leaf[r] x_leaf.
+    Each V^T x is formed only for nodes that hold a requested row."""
+    X = np.asarray(X, dtype=np.float64)
+    vec = X.ndim == 1
+    if vec:
+        X = X.reshape(-1, 1)
+    if absval:
+        X = np.abs(X)
+    f = np.abs if absval else (lambda a: a)
+    U, V, D = _factors(h, stored)
+    rows = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((len(rows), X.shape[1]))
+    for k in range(1, h.depth + 1):
+        for i, (s, m) in enumerate(h.levels[k]):
+            sel = np.nonzero((rows >= s) & (rows < s + m))[0]
+            if len(sel) == 0:
+                continue
+            s1, m1 = h.levels[k][i ^ 1]
+            y = f(V[k][i ^ 1]).T @ X[s1:s1 + m1]
+            out[sel] += f(U[k][i])[rows[sel] - s] @ y
+    for i, (s, m) in enumerate(h.levels[h.depth]):
+        sel = np.nonzero((rows >= s) & (rows < s + m))[0]
+        if len(sel):
+            out[sel] += f(D[i])[rows[sel] - s] @ X[s:s + m]
+    return out[:, 0] if vec else out
+
+
+def hodlr_matvec_rows(h, X, rows, stored: bool = True) -> np.ndarray:
+    """Rows ``rows`` of H-hat X (fp64), for products too large to form in
+    full on the host; equals ``hodlr_matvec(h, X)[rows]`` up to the order of
+    the fp64 sums."""
+    return _rows_product(h, X, rows, stored, absval=False)
+
+
+def abs_product_rows(h, X, rows, stored: bool = True) -> np.ndarray:
+    """Rows ``rows`` of ``abs_product(h, X)``."""
+    return _rows_product(h, X, rows, stored, absval=True)
+
+
 def _add(a, b, work):
     if work == "fp64":
         return a + b

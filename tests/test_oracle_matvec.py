@@ -144,3 +144,20 @@ def test_fig_4_2_qualitative(name):
     # fp32 floors near u(fp32): at eps = 1e-10 < u it is far above the fp64 error
     assert errs[("fp32", 1e-10)] > 10 * errs[("fp64", 1e-10)]
     assert errs[("fp32", 1e-10)] < 1e3 * F.unit_roundoff("fp32")
+
+
+@pytest.mark.parametrize("n,depth,R", [(1000, 4, 3), (777, 5, 1), (512, 3, 8)])
+def test_sampled_rows_equal_the_dense_product(n, depth, R):
+    """The sampled-row product (used where the full product is too large for
+    the host) equals the dense assembly's rows times x, and its |.| twin the
+    rows of abs_product; rows include both ends of leaves and of the matrix."""
+    spec = synth.KernelSpec(K.GAUSS, len2=0.01, diag=1e-2)
+    h, _A = _build(n, depth, 1e-6, spec)
+    X = synth.rhs_normal(n, R, 9, np.float64)
+    rng = np.random.default_rng(4)
+    ends = [s for (s, m) in h.levels[h.depth]] + [s + m - 1 for (s, m) in h.levels[h.depth]]
+    rows = np.unique(np.concatenate([rng.integers(0, n, 40), ends, [0, n - 1]]))
+    ref = M.assemble(h)[rows] @ X
+    got = M.hodlr_matvec_rows(h, X, rows)
+    assert np.allclose(got, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    assert np.allclose(M.abs_product_rows(h, X, rows), M.abs_product(h, X)[rows], rtol=1e-13, atol=0)
