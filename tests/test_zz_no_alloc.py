@@ -52,8 +52,9 @@ def test_noalloc_matches_matvec_twice(lib, work, R):
     exact = M.hodlr_matvec(h, X64)
     g_abs = M.abs_product(h, X64)
     tol = (Bd.gamma(M.max_chain(h), u) + 2 * u) * g_abs + u * np.abs(exact)
-    # the reference product (hodlr_matvec) runs its leaf products on the
-    # tensor cores from 16 fp32 columns on (three tf32 products)
+    # the reference product (hodlr_matvec) runs its leaf products and the
+    # fp32 V^T X on the tensor cores from 16 fp32 columns on (tf32 products
+    # of the hi/lo split of both factors)
     tol_ref = tol if (work != "fp32" or R < 16) else \
         (Bd.gamma(M.max_chain(h), 2 * u) + 14 * u) * g_abs + u * np.abs(exact)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
