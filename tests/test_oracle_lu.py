@@ -2,8 +2,9 @@
 textbook example, the block LU without truncation equal to the dense LU,
 Assumption 3.6 for the Schur-complement truncation, Cor. 3.11's backward
 error bound with truncation, the triangular solves and fp64-residual
-iterative refinement to a 1e-12 backward error, and a planted mistake (the
-Schur update dropped) that the pins catch."""
+iterative refinement to a 1e-12 backward error, GMRES (exact after n steps)
+and GMRES-IR with a coarse LU, and a planted mistake (the Schur update
+dropped) that the pins catch."""
 import numpy as np
 import pytest
 
@@ -113,3 +114,28 @@ def test_planted_dropped_schur_update_is_caught(monkeypatch):
     monkeypatch.setattr(LU, "solve_triangular", no_u12)
     L, U = LU.hodlr_lu(Hh, h.levels, 0.0)
     assert not np.allclose(L @ U, Hh, rtol=0, atol=1e-13 * np.abs(Hh).max())
+
+
+def test_gmres_is_exact_after_n_steps_without_preconditioner():
+    """Unpreconditioned GMRES on an n x n system reaches the solution in at
+    most n Arnoldi steps (Krylov space = R^n)."""
+    rng = np.random.default_rng(1)
+    n = 30
+    A = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    b = rng.standard_normal(n)
+    x, steps = LU.gmres(lambda v: A @ v, b, tol=1e-13, restart=n)
+    assert steps <= n
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10, atol=1e-10)
+
+
+def test_gmres_ir_with_a_coarse_lu_reaches_1e_12():
+    """NEXT-2's target on four right-hand sides: the HODLR LU truncated at
+    eps = 1e-2 as GMRES preconditioner, fp64 residuals: backward error
+    <= 1e-12 within a few refinement steps, few GMRES steps each."""
+    n, depth = 512, 4
+    h, A = _hodlr(n, depth, 1e-2)
+    L, U = LU.hodlr_lu(M.assemble(h), h.levels, 1e-2)
+    B = synth.rhs_normal(n, 4, 7, np.float64)
+    X, hist, inner = LU.gmres_ir(A, L, U, B, tol=1e-12)
+    assert hist[-1] <= 1e-12 and len(hist) <= 5
+    assert max(inner) <= 30
