@@ -57,23 +57,35 @@ MAX_NRHS = 64         # the handle's max_nrhs in this benchmark
 
 # DRAM bytes (read + written) per step of each product kernel, summed over
 # the step's launches of the kernel, from one ncu capture of this benchmark
-# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
-# library's CUDA sources are the ones they were measured on (their SHA-256),
-# else null.
-TRAFFIC_SRC_SHA = "b656b9bdbd2ed1ca04e7798e3ba85a1c47672fb5b3406182299803667cf6a4a1"
-TRAFFIC_PER_STEP = {"matvec_kernel": 202904793, "leaf_tc_kernel": 96994541}   # bytes per step
+# (dram__bytes_read.sum + dram__bytes_write.sum); each figure is reported
+# only while the sources that define its kernel are the ones it was measured
+# on (SHA-256 of those files), else null.
+TRAFFIC_PER_STEP = {
+    "matvec_kernel": (("hodlr_internal.cuh", "matvec.cu"),
+                      "503da171ca0cc8fbfb5ca2f9f6a5b49cac41fcbd8f200e381c11c7cb117d6c45", 202904793),
+    "leaf_tc_kernel": (("hodlr_internal.cuh", "leaf_tc.cu"),
+                       "36544c3200dfa7821dbaaf762a0247beeff9c1f49754393a9b623b89a65fcbb8", 96994541),
+}
 
 
-def _csrc_sha():
+def _src_sha(files):
     import hashlib
     d = os.path.join(ROOT, "paper_2407_21637_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in files:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
+
+
+def traffic_per_step(kernel):
+    """The measured DRAM bytes per step of `kernel`, or None when its sources changed since."""
+    entry = TRAFFIC_PER_STEP.get(kernel)
+    if entry is None:
+        return None
+    files, sha, nbytes = entry
+    return nbytes if _src_sha(files) == sha else None
 
 
 def max_over_ranks(x, dist, device):
@@ -423,7 +435,7 @@ def run_ours(args, rank, world, dist):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": dominant,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (TRAFFIC_PER_STEP.get(dominant) if TRAFFIC_SRC_SHA == _csrc_sha() else None),
+                     "traffic": traffic_per_step(dominant),
                      "traffic_per": "step (the kernel's launches of one step, like achieved)",
                      "peak_source": peak_kind,
                      "bytes_per_launch": "algorithmic bytes of each launch of the kernel (factors, leaves, "

@@ -20,9 +20,9 @@
 // product is tested against.
 //
 // Per CTA (persistent, one per SM): sixteen converter warps keep a ring of
-// six stages with cp.async: a K-chunk of 32 columns of A for 128 rows
-// (placed in the 128-byte-swizzled K-major layout) and the matching 32 rows
-// of X.  Once a chunk has landed they split it: A's hi and lo parts go to
+// three stages with cp.async: a K-chunk of 64 columns of A for 128 rows
+// (placed in the 128-byte-swizzled K-major layout, two atoms along K) and
+// the matching 64 rows of X.  Once a chunk has landed they split it: A's hi and lo parts go to
 // tensor memory (tcgen05.st, lane = row), X is transposed into N x 32 hi
 // and lo tiles in shared memory (two operand buffers each).  One thread
 // issues the MMAs (tcgen05.mma.kind::tf32, A from tensor memory, B from a
@@ -45,7 +45,8 @@ constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kEpiWarps = 4;                    // one per TMEM lane quadrant
 constexpr int kTcThreads = kConvThreads + 32 + 32 * kEpiWarps;   // converters, the MMA warp, epilogue
 constexpr int kTcM = 128;                       // rows per group (MMA M)
-constexpr int kKc = 32;                         // K-chunk: 32 fp32 = one 128-byte swizzle row
+constexpr int kKc = 64;                         // K-chunk: 64 fp32 = two 128-byte swizzle atoms along K
+constexpr int kKa = kKc / 32;                   // swizzle atoms along K per chunk
 constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -102,6 +103,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 __device__ __forceinline__ uint32_t sw128(int r, int g) {
   return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((g ^ (r & 7)) << 4));
 }
+// The same for a chunk of kKc values per row: atom column g / 8 (32 values
+// of K for all `rows` rows), then sw128 within it.
+__device__ __forceinline__ uint32_t swk(int r, int g, int rows) {
+  return (uint32_t)((g >> 3) * rows * 128) + sw128(r, g & 7);
+}
 // x rounded to tf32 (10 fraction bits) to nearest, ties away from zero, on
 // the bit pattern: half a unit of the 13 dropped bits is added to the
 // magnitude and the dropped bits are cleared (a carry into the exponent is
@@ -127,11 +133,14 @@ __device__ __forceinline__ void mma_tf32_tmem_a(uint32_t tmem_d, uint32_t tmem_a
       "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// 8 consecutive 32-bit columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-               : "memory");
+// 16 consecutive 32-bit columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
@@ -179,18 +188,18 @@ __device__ __forceinline__ float lds1f(uint32_t a) {
 }
 
 // Shared memory (every part 1024-byte aligned):
-//  raw ring, kTcRaw stages: A (128 x 32 fp32, placed by cp.async in the
-//    128-byte-swizzled K-major layout) and X (32 x N fp32, row-major as
-//    loaded);
-//  two operand buffers B_hi, B_lo (X^T, N x 32 tf32, K-major, 128-byte
+//  raw ring, kTcRaw stages: A (128 x 64 fp32, placed by cp.async in the
+//    128-byte-swizzled K-major layout, two atom columns of 32 values) and X
+//    (64 x N fp32, row-major as loaded);
+//  two operand buffers [X_hi | X_lo]^T (2N rows x 64 tf32, K-major, 128-byte
 //    swizzle).
 // Tensor memory (512 columns): two accumulators of 2N columns (columns
 // 128 a: the products with X_hi in the first N, with X_lo in the next N)
-// and two A operand buffers (columns kTmemA + 64 b: A_hi in 32 columns,
-// A_lo in the next 32; lane = row of A).
-constexpr int kTcRaw = 6;
+// and two A operand buffers (columns kTmemA + 128 b: A_hi in 64 columns,
+// A_lo in the next 64; lane = row of A).
+constexpr int kTcRaw = 3;
 constexpr uint32_t kTmemAcc = 128;
-constexpr uint32_t kTmemA = 2 * kTmemAcc;
+constexpr uint32_t kTmemA = 2 * kTmemAcc;        // A buffer b: hi at kTmemA + 2 kKc b, lo kKc columns further
 constexpr uint32_t kTmemCols = 512;
 __host__ __device__ inline uint32_t tc_raw_bytes(int N) { return (uint32_t)kTcM * kKc * 4 + (uint32_t)N * kKc * 4; }
 __host__ __device__ inline uint32_t tc_op_bytes(int N) { return 2u * (uint32_t)N * kKc * 4; }
@@ -261,9 +270,8 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ c
     constexpr int kAP = kTcM / kAR;         // A pieces per thread
     static_assert(kAP * kAR == kTcM && kAR % 32 == 0, "converter threads must tile the 128 A rows");
     const int rr = t >> 3, cg = t & 7;
-    const uint32_t so0 = sw128(rr, cg);   // + kAR * 128 * i for piece i
     // A split: warp w takes TMEM lanes 32 (w % 4) .. + 31 (row = lane) and
-    // columns 8 (w / 4) .. + 7 of the chunk
+    // columns 16 (w / 4) .. + 15 of the chunk
     static_assert(kConvWarps == 16, "four warps per TMEM lane quadrant");
     const int aq = warp & 3, akq = warp >> 2;
     const int arow = 32 * aq + lane;
@@ -286,12 +294,17 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ c
       if (u < total) {
         const int k0 = lkc * kKc;
         const uint32_t ra = raw0 + (uint32_t)(u % kTcRaw) * rb, rx = ra + ab;
-        const bool kin = 4 * cg + k0 < ((lm + 3) & ~3);
+        const int lmp = (lm + 3) & ~3;
 #pragma unroll
-        for (int i = 0; i < kAP; ++i) {
-          const bool ok = aoff[i] >= 0 && kin;
-          cp_async16(ra + so0 + (uint32_t)(kAR * 128) * i,
-                     ok ? (const void*)(pool + aoff[i] + (size_t)(k0 + 4 * cg) * 4) : (const void*)pool, ok ? 16u : 0u);
+        for (int a = 0; a < kKa; ++a) {
+          const int gk = cg + 8 * a;   // 16-byte group of the chunk
+          const bool kin = 4 * gk + k0 < lmp;
+#pragma unroll
+          for (int i = 0; i < kAP; ++i) {
+            const bool ok = aoff[i] >= 0 && kin;
+            cp_async16(ra + swk(rr + kAR * i, gk, kTcM),
+                       ok ? (const void*)(pool + aoff[i] + (size_t)(k0 + 4 * gk) * 4) : (const void*)pool, ok ? 16u : 0u);
+          }
         }
         const float* xbase = X + (int64_t)lxrow * ldx;
 #pragma unroll
@@ -347,19 +360,18 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ c
       // group's valid rows is skipped; rows past them in a quadrant reach
       // only accumulator rows that the epilogue does not write)
       if (32 * aq < crows) {
-        const uint4 v0 = lds16(ra + sw128(arow, 2 * akq)), v1 = lds16(ra + sw128(arow, 2 * akq + 1));
-        uint32_t h[8], l[8];
-        split(__uint_as_float(v0.x), h[0], l[0]);
-        split(__uint_as_float(v0.y), h[1], l[1]);
-        split(__uint_as_float(v0.z), h[2], l[2]);
-        split(__uint_as_float(v0.w), h[3], l[3]);
-        split(__uint_as_float(v1.x), h[4], l[4]);
-        split(__uint_as_float(v1.y), h[5], l[5]);
-        split(__uint_as_float(v1.z), h[6], l[6]);
-        split(__uint_as_float(v1.w), h[7], l[7]);
-        const uint32_t ta = tmem + alane + kTmemA + 64u * (uint32_t)b + 8u * (uint32_t)akq;
-        tmem_st8(ta, h);
-        tmem_st8(ta + 32, l);
+        uint32_t h[16], l[16];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint4 v = lds16(ra + swk(arow, 4 * akq + j, kTcM));
+          split(__uint_as_float(v.x), h[4 * j + 0], l[4 * j + 0]);
+          split(__uint_as_float(v.y), h[4 * j + 1], l[4 * j + 1]);
+          split(__uint_as_float(v.z), h[4 * j + 2], l[4 * j + 2]);
+          split(__uint_as_float(v.w), h[4 * j + 3], l[4 * j + 3]);
+        }
+        const uint32_t ta = tmem + alane + kTmemA + 2u * kKc * (uint32_t)b + 16u * (uint32_t)akq;
+        tmem_st16(ta, h);
+        tmem_st16(ta + kKc, l);
       }
       // B = X^T: thread (n, k-group of 4), consecutive threads take consecutive n
 #pragma unroll
@@ -370,9 +382,8 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ c
           uint32_t h[4], l[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) split(lds1f(rx + (uint32_t)(((4 * kg + e) * N + n) * 4)), h[e], l[e]);
-          const uint32_t o = sw128(n, kg);
-          sts4(oa + o, h[0], h[1], h[2], h[3]);
-          sts4(oa + xb + o, l[0], l[1], l[2], l[3]);
+          sts4(oa + swk(n, kg, 2 * N), h[0], h[1], h[2], h[3]);
+          sts4(oa + swk(N + n, kg, 2 * N), l[0], l[1], l[2], l[3]);
         }
       }
       // TMEM stores complete, generic-proxy stores -> visible to the tensor
@@ -408,11 +419,12 @@ leaf_tc_kernel(const TcGroup* __restrict__ groups, const int32_t* __restrict__ c
         if (ok && !*(volatile int*)abort_flag) {
           tc_fence_after();
           const uint32_t oa = op0 + (uint32_t)b * ob;
-          const uint32_t ah = tmem + kTmemA + 64u * (uint32_t)b, al = ah + 32;
-          const uint64_t bd = desc_sw128(oa);   // 2N rows: X_hi^T, then X_lo^T
+          const uint32_t ah = tmem + kTmemA + 2u * kKc * (uint32_t)b, al = ah + kKc;
 #pragma unroll
           for (int ks = 0; ks < kKc / 8; ++ks) {
-            const uint64_t adv = (uint64_t)(ks * 32) >> 4;   // 8 tf32 = 32 bytes along K
+            // 2N rows: X_hi^T, then X_lo^T; atom column ks / 4, 8 tf32 = 32 bytes along K within it
+            const uint64_t bd = desc_sw128(oa + (uint32_t)((ks >> 2) * 2 * N * 128));
+            const uint64_t adv = (uint64_t)((ks & 3) * 32) >> 4;
             const uint32_t ac = (uint32_t)(ks * 8);          // 8 tf32 = 8 TMEM columns
             mma_tf32_tmem_a(acc, ah + ac, bd + adv, idesc, (ckc > 0 || ks > 0) ? 1u : 0u);
             mma_tf32_tmem_a(acc, al + ac, bd + adv, idesc, 1u);
