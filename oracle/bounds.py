@@ -13,8 +13,10 @@ Test infrastructure (see ``oracle/__init__``).
 * HODLR LU backward error (Cor. 3.11, when u <~ eps/n):
       ||Delta H||_F <~ 2 (2^l - 1) eps ||H||_F + 11 (2^l - 1) eps ||L^||_F ||U^||_F
 
-Parity: these are the printed formulas; they are checked against the oracle's
-own computations (which must satisfy them), not against themselves.
+Parity: pinned.  Each function is compared with its value worked out by hand
+at fixed arguments (``tests/test_oracle_kernels_bounds.py``), so a changed
+constant fails; the oracle's own computations are also checked to satisfy
+the bounds (tests of compress, matvec and lu).
 """
 from __future__ import annotations
 

@@ -15,7 +15,10 @@ paper kernels (i) and (ii) then get their stated diagonals 1 and 0 through
 ``diag``.  Off the diagonal, coincident points of a singular kernel would give
 inf; the workloads never produce them.
 
-Parity: pinned by direct formula tests on hand-computed entries.
+Parity: pinned.  Every kind is compared with entries evaluated by hand at
+fixed 1D and 2D points (diagonal rules included) in
+``tests/test_oracle_kernels_bounds.py``; planted mistakes (a doubled length
+scale, a dropped diagonal term) fail those pins.
 """
 from __future__ import annotations
 
