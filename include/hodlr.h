@@ -154,7 +154,7 @@ typedef struct {
  * matrix on the GPU (Algorithm 3.2): every off-diagonal block is compressed
  * to relative Frobenius accuracy eps (Def. 2.3) by a randomized range finder
  * whose matrix entries are generated in registers (never stored): sketch
- * Y = A_b Omega, Q = orth(Y) (shifted Cholesky QR + two Cholesky QR passes),
+ * Y = A_b Omega, Q = orth(Y) (classical Gram-Schmidt applied twice),
  * B = Q^T A_b, the sketch residual ||A_b - Q Q^T A_b||_F computed from
  * regenerated entries, and a one-sided Jacobi SVD of B's triangular factor;
  * the rank is the smallest r whose SVD tail plus sketch residual is within
@@ -206,20 +206,26 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
  * paper has no counterpart; this is a library convenience.
  *
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call)
- * and does not use the handle's own scratch: its scratch is one 4 MiB device
+ * and does not use the handle's own scratch: its scratch is one 1 MiB device
  * array inside this library, which every GPU that loads the library holds
- * until the process exits.  Arguments and results are those of hodlr_matvec
- * (same kernels, same summation order, bitwise the same B).  Right-hand sides
- * are processed in batches that fit the array; a matrix whose per-column
- * scratch (its V^T X results and partial sums, about 8 bytes per rank column
- * per node and work item) does not fit at all is rejected with HODLR_EINVAL.
+ * until the process exits.  Arguments and results are those of
+ * hodlr_matvec.  It always runs the CUDA-core product, in batches of columns
+ * that fit the array (at most as many as hodlr_matvec takes per launch).
+ * Where hodlr_matvec takes the CUDA-core path with the same batches (fp64
+ * work; fp32 work with fewer than 16 columns) and the array holds a whole
+ * batch, B is bitwise the same; fp32 products of 16 or more columns, which
+ * hodlr_matvec runs on the tensor cores, and products split into narrower
+ * batches agree within the rounding bound of the products.  A matrix whose
+ * per-column scratch (its partial V^T X sums: about one value per rank
+ * column, per node and per SM that holds rows of the node) does not fit at
+ * all is rejected with HODLR_EINVAL before anything is enqueued.
  *
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
- * Every call on every handle shares the array and the array keeps the last
- * call's contents: the call clears what must start at zero itself, and calls
- * that overlap in time on the GPU (different streams, threads or handles)
- * race on the array and must be serialised by the caller. */
+ * The current device must be the handle's device (HODLR_EINVAL otherwise):
+ * the array's device address is looked up on the current device on every
+ * call.  Every call on every handle shares the array and the array keeps
+ * the last call's contents: the call clears what must start at zero itself,
+ * and calls that overlap in time on the GPU (different streams, threads or
+ * handles) race on the array and must be serialised by the caller. */
 hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
                                   void* B, int64_t ldb, int32_t xb_prec, void* stream);
 

@@ -308,16 +308,22 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       }
     }
   }
-  // tiles
+  // tiles: header and U rows (U area), leaf-block rows (D area) and V rows
+  // (V area), each area in tile order so that the parts of consecutive
+  // tiles are contiguous
   h->p2.clear();
   std::vector<std::pair<int64_t, uint32_t>> headers;   // (byte offset in pool, word)
   int max_nq = 0, max_region = 0;
-  std::vector<int> leaf_nq(nleaves, 0), leaf_yrow(nleaves, 0);
+  std::vector<int> leaf_nq(nleaves, 0), leaf_yrow(nleaves, 0), leaf_tile0(nleaves + 1, 0);
+  std::vector<std::vector<int>> leaf_anc(nleaves), leaf_vseg(nleaves);
   int yrows = 0;
+  const int hbytes = (int)align_up((size_t)8 * depth, 16);   // one header entry per level
+  pool = align_up(pool, 256);
   for (int l = 0; l < nleaves; ++l) {
     const LeafDev& lf = h->leaves[l];
     // the leaf's U columns: ancestors level 1..depth, columns 0..rU-1
-    std::vector<int> anc(depth + 1, 0);
+    std::vector<int>& anc = leaf_anc[l];
+    anc.assign(depth + 1, 0);
     int nq = 0;
     for (int k = 1; k <= depth; ++k) {
       anc[k] = node_index(k, l >> (depth - k));
@@ -327,27 +333,29 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     leaf_yrow[l] = yrows;
     yrows += (int)align_up(nq, 4);               // 16-byte aligned blocks in fp32 and fp64
     max_nq = std::max(max_nq, nq);
-    const int hbytes = (int)align_up((size_t)8 * depth, 16);   // one header entry per level
     const int mp = (int)align_up(lf.m, 4);                // D row length (zero padded)
     const int dbytes = mp * kTileRows * ebw;
-    // byte offset of each level's U segment inside the U area
+    // byte offset of each level's U (V) block after the header (inside the V part)
     std::vector<int> useg(depth + 2, 0);
+    std::vector<int>& vseg = leaf_vseg[l];
+    vseg.assign(depth + 2, 0);
     for (int k = 1; k <= depth; ++k) {
       const NodeDev& a = h->nodes[anc[k]];
       useg[k + 1] = useg[k] + (int)align_up((size_t)a.rU * kTileRows * prec_bytes(a.tierU), 16);
+      vseg[k + 1] = vseg[k] + (int)align_up((size_t)a.rV * kTileRows * prec_bytes(a.tierV), 16);
     }
     const int ubytes = useg[depth + 1];
-    const int region = hbytes + ubytes + dbytes;
     max_region = std::max(max_region, dbytes);
+    leaf_tile0[l] = (int)h->p2.size();
     for (int t0 = 0; t0 < lf.m; t0 += kTileRows) {
-      pool = align_up(pool, 128);
       P2Tile tl;
       memset(&tl, 0, sizeof(tl));
       tl.off = (int64_t)pool;
-      tl.bytes = region;
+      tl.bytes = hbytes + ubytes;
       tl.hbytes = hbytes;
       tl.ubytes = ubytes;
       tl.dbytes = dbytes;
+      tl.vbytes = vseg[depth + 1];
       tl.m = lf.m;
       tl.rows = std::min(kTileRows, lf.m - t0);
       tl.row0 = lf.row0 + t0;
@@ -356,16 +364,12 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       tl.yrow = leaf_yrow[l];
       h->p2.push_back(tl);
       // header, two words per level k = 1..depth: byte offset of the level's
-      // U block inside the U area; rank | format << 16
+      // U block after the header; rank | format << 16
       for (int k = 1; k <= depth; ++k) {
         const NodeDev& a = h->nodes[anc[k]];
         headers.push_back({tl.off + 8 * (k - 1), (uint32_t)useg[k]});
         headers.push_back({tl.off + 8 * (k - 1) + 4, (uint32_t)a.rU | ((uint32_t)a.tierU << 16)});
       }
-      // D[t0:t0+32, j] for every column j (row-major, row stride mp)
-      for (int j = 0; j < lf.m; ++j)
-        h->tasks.push_back({h->st_D[l] + (int64_t)t0 * lf.m + j, lf.m, tl.rows, kTileRows,
-                            tl.off + hbytes + ubytes + (int64_t)j * ebw, h->work, mp * ebw, 1.0});
       // U_a[rows of this tile, c] for every ancestor a and column c (column
       // by column: 32 consecutive rows per column)
       for (int k = 1; k <= depth; ++k) {
@@ -377,7 +381,72 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
           h->tasks.push_back({h->st_U[q] + (int64_t)rel * a.rU + c, a.rU, tl.rows, kTileRows,
                               tl.off + hbytes + useg[k] + (int64_t)c * kTileRows * eb, a.tierU, 0, sU[q]});
       }
-      pool += region;
+      pool += (size_t)tl.bytes;
+    }
+  }
+  leaf_tile0[nleaves] = (int)h->p2.size();
+  const int n_tiles = (int)h->p2.size();
+  std::vector<int> tile_leaf(n_tiles, 0);
+  for (int l = 0; l < nleaves; ++l)
+    for (int t = leaf_tile0[l]; t < leaf_tile0[l + 1]; ++t) tile_leaf[t] = l;
+  // D area
+  pool = align_up(pool, 256);
+  for (int l = 0; l < nleaves; ++l) {
+    const LeafDev& lf = h->leaves[l];
+    const int mp = (int)align_up(lf.m, 4);
+    for (int t = leaf_tile0[l]; t < leaf_tile0[l + 1]; ++t) {
+      P2Tile& tl = h->p2[t];
+      pool = align_up(pool, 128);
+      tl.doff = (int64_t)pool;
+      const int t0 = tl.row0 - lf.row0;
+      // D[t0:t0+32, j] for every column j (row-major, row stride mp)
+      for (int j = 0; j < lf.m; ++j)
+        h->tasks.push_back({h->st_D[l] + (int64_t)t0 * lf.m + j, lf.m, tl.rows, kTileRows,
+                            tl.doff + (int64_t)j * ebw, h->work, mp * ebw, 1.0});
+      pool += (size_t)tl.dbytes;
+    }
+  }
+  // V area (streamed product only; the node-ordered V columns above stay the
+  // copy that export, save and the tensor-core V groups read): per tile and
+  // level a block of 32 rows x rank, column by column, rows past the tile zero
+  pool = align_up(pool, 256);
+  h->tasks_v.clear();
+  for (int l = 0; l < nleaves; ++l) {
+    const LeafDev& lf = h->leaves[l];
+    for (int t = leaf_tile0[l]; t < leaf_tile0[l + 1]; ++t) {
+      P2Tile& tl = h->p2[t];
+      tl.voff = (int64_t)pool;
+      const int t0 = tl.row0 - lf.row0;
+      for (int k = 1; k <= depth; ++k) {
+        const int q = leaf_anc[l][k];
+        const NodeDev& a = h->nodes[q];
+        const int eb = prec_bytes(a.tierV);
+        const int rel = lf.row0 - a.row0 + t0;
+        for (int c = 0; c < a.rV; ++c)
+          h->tasks_v.push_back({h->st_V[q] + (int64_t)rel * a.rV + c, a.rV, tl.rows, kTileRows,
+                                tl.voff + leaf_vseg[l][k] + (int64_t)c * kTileRows * eb, a.tierV, 0, sV[q]});
+      }
+      pool += (size_t)tl.vbytes;
+    }
+  }
+  // D2 area (streamed product): each tile's leaf block once more, in
+  // 16-byte chunks of consecutive columns, chunk q of row r at (q * 32 + r) * 16
+  pool = align_up(pool, 256);
+  {
+    const int g16 = 16 / ebw;   // columns per chunk
+    for (int l = 0; l < nleaves; ++l) {
+      const LeafDev& lf = h->leaves[l];
+      for (int t = leaf_tile0[l]; t < leaf_tile0[l + 1]; ++t) {
+        P2Tile& tl = h->p2[t];
+        tl.d2off = (int64_t)pool;
+        tl.d2bytes = (lf.m + g16 - 1) / g16 * kTileRows * 16;
+        const int t0 = tl.row0 - lf.row0;
+        for (int j = 0; j < lf.m; ++j)
+          h->tasks_v.push_back({h->st_D[l] + (int64_t)t0 * lf.m + j, lf.m, tl.rows, kTileRows,
+                                tl.d2off + (int64_t)(j / g16) * kTileRows * 16 + (int64_t)(j % g16) * ebw, h->work,
+                                16, 1.0});
+        pool += (size_t)tl.d2bytes;
+      }
     }
   }
   // tensor-core groups: up to four consecutive tiles (128 rows) of a leaf
@@ -392,7 +461,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     gr.vtab = -1;   // a leaf group
     while (t < h->p2.size() && gr.ntl < 4 && h->p2[t].xrow0 == t0.xrow0) {
       const P2Tile& tt = h->p2[t];
-      gr.doff[gr.ntl++] = tt.off + tt.hbytes + tt.ubytes;
+      gr.doff[gr.ntl++] = tt.doff;
       gr.rows += tt.rows;
       ++t;
     }
@@ -408,6 +477,14 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     CK(cudaMemcpyAsync(d_tasks.p, h->tasks.data(), h->tasks.size() * sizeof(PackTask),
                        cudaMemcpyHostToDevice, s));
     CK(launch_pack(d_stage, (const PackTask*)d_tasks.p, (int)h->tasks.size(), h->d_pool, s));
+    if (!h->tasks_v.empty()) {
+      DevBuf d_tv;
+      CK(cudaMalloc(&d_tv.p, h->tasks_v.size() * sizeof(PackTask)));
+      CK(cudaMemcpyAsync(d_tv.p, h->tasks_v.data(), h->tasks_v.size() * sizeof(PackTask),
+                         cudaMemcpyHostToDevice, s));
+      CK(launch_pack(d_stage, (const PackTask*)d_tv.p, (int)h->tasks_v.size(), h->d_pool, s));
+      CK(cudaStreamSynchronize(s));
+    }
     std::vector<int64_t> hoff(headers.size());
     std::vector<uint32_t> hval(headers.size());
     for (size_t e = 0; e < headers.size(); ++e) { hoff[e] = headers[e].first; hval[e] = headers[e].second; }
@@ -609,6 +686,184 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     tcv.swap(tcv2);
   }
 
+  // ---- streamed product: tiles dealt to the CTAs in contiguous ranges of
+  //      about equal bytes, the partial slots of every node (one per CTA
+  //      that covers it, in CTA order), the per-(tile, level) table and the
+  //      Y items every CTA reduces for itself ----
+  int st_grid = 1;
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&st_grid, cudaDevAttrMultiProcessorCount, dev));
+    st_grid = std::max(st_grid, 1);
+  }
+  std::vector<int32_t> st_cta_t0(st_grid + 1, 0), cta_of(n_tiles, 0);
+  {
+    std::vector<int64_t> pre(n_tiles + 1, 0);
+    for (int t = 0; t < n_tiles; ++t)
+      pre[t + 1] = pre[t] + h->p2[t].vbytes + h->p2[t].bytes + h->p2[t].dbytes;
+    for (int c = 1; c < st_grid; ++c) {
+      const double target = (double)pre[n_tiles] * c / st_grid;
+      int t = (int)(std::lower_bound(pre.begin(), pre.end(), (int64_t)std::ceil(target)) - pre.begin());
+      if (t > 0 && target - (double)pre[t - 1] < (double)pre[std::min(t, n_tiles)] - target) --t;
+      st_cta_t0[c] = std::min(std::max(t, st_cta_t0[c - 1]), n_tiles);
+    }
+    st_cta_t0[st_grid] = n_tiles;
+    for (int c = 0; c < st_grid; ++c)
+      for (int t = st_cta_t0[c]; t < st_cta_t0[c + 1]; ++t) cta_of[t] = c;
+  }
+  // slot of every (tile, level): the rank of the tile's CTA among the CTAs
+  // holding tiles of the level-k ancestor (CTAs without tiles take none)
+  std::vector<int> st_nslots(nnodes, 0), st_pslot0(nnodes, -1);
+  std::vector<int> tile_slot((size_t)n_tiles * std::max(depth, 1), 0);
+  int st_p_rows = 0, st_max_rank = 0;
+  for (int k = 1; k <= depth; ++k) {
+    const int span = 1 << (depth - k);
+    for (int i = 0; i < (1 << k); ++i) {
+      const int q = node_index(k, i);
+      const NodeDev& nd = h->nodes[q];
+      st_max_rank = std::max(st_max_rank, nd.rV);
+      int ns = 0, last = -1;
+      for (int t = leaf_tile0[i * span]; t < leaf_tile0[(i + 1) * span]; ++t) {
+        if (cta_of[t] != last) {
+          last = cta_of[t];
+          ++ns;
+        }
+        tile_slot[(size_t)t * depth + (k - 1)] = ns - 1;
+      }
+      st_nslots[q] = ns;
+      if (nd.rV == 0) continue;
+      st_pslot0[q] = st_p_rows;
+      st_p_rows += ns * nd.rV;
+    }
+  }
+  std::vector<int32_t> st_accoff(depth + 1, 0);
+  int st_acc_rows = 0;
+  for (int k = 1; k <= depth; ++k) {
+    int mx = 0;
+    for (int i = 0; i < (1 << k); ++i) mx = std::max(mx, h->nodes[node_index(k, i)].rV);
+    st_accoff[k] = st_acc_rows;
+    st_acc_rows += mx;
+  }
+  std::vector<StLev> stlev;   // per (CTA, leaf of the CTA, level)
+  std::vector<hodlr::StTile> st_tile(n_tiles);
+  std::vector<YItem> st_y;
+  std::vector<hodlr::RTask> st_task;
+  std::vector<hodlr::StCta> st_cta(st_grid);
+  int st_y_rows = 0, st_red_rows = 0, st_max_tiles = 0, st_max_leaves = 0, st_max_vbytes = 0, st_max_cta_v = 0;
+  int st_max_cta_xrows = 0, st_max_tile_bytes = 0, st_max_cta_u = 0, st_max_ubytes = 0, st_max_d2bytes = 0;
+  for (int c = 0; c < st_grid; ++c) {
+    hodlr::StCta& sc = st_cta[c];
+    memset(&sc, 0, sizeof(sc));
+    sc.t0 = st_cta_t0[c];
+    sc.nt = st_cta_t0[c + 1] - st_cta_t0[c];
+    if (sc.nt > 0) {
+      const P2Tile& a = h->p2[sc.t0];
+      const P2Tile& b = h->p2[sc.t0 + sc.nt - 1];
+      sc.voff = a.voff;
+      sc.vbytes = (int)(b.voff + b.vbytes - a.voff);
+      sc.uoff = a.off;
+      sc.ubytes = (int)(b.off + b.bytes - a.off);
+      sc.xrow0 = a.row0;
+      sc.xrows = b.row0 + b.rows - a.row0;
+    }
+    st_max_tiles = std::max(st_max_tiles, sc.nt);
+    st_max_cta_v = std::max(st_max_cta_v, sc.vbytes);
+    st_max_cta_xrows = std::max(st_max_cta_xrows, sc.xrows);
+    st_max_cta_u = std::max(st_max_cta_u, sc.ubytes);
+    sc.y0 = (int32_t)st_y.size();
+    std::map<int, int> yrow_of;   // needed node -> its first row in this CTA's Y area
+    int ycount = 0;
+    std::vector<YItem> items;
+    sc.l0 = depth > 0 ? (int32_t)(stlev.size() / depth) : 0;
+    int nl = 0, last_leaf = -1;
+    for (int t = st_cta_t0[c]; t < st_cta_t0[c + 1]; ++t) {
+      const P2Tile& tl = h->p2[t];
+      st_max_vbytes = std::max(st_max_vbytes, tl.vbytes);
+      st_max_tile_bytes = std::max(st_max_tile_bytes, tl.bytes + tl.d2bytes);
+      st_max_ubytes = std::max(st_max_ubytes, tl.bytes);
+      st_max_d2bytes = std::max(st_max_d2bytes, tl.d2bytes);
+      const int l = tile_leaf[t];
+      hodlr::StTile& rec = st_tile[t];
+      memset(&rec, 0, sizeof(rec));
+      rec.voff = tl.voff;
+      rec.uoff = tl.off;
+      rec.d2off = tl.d2off;
+      rec.vbytes = tl.vbytes;
+      rec.ubytes = tl.bytes;
+      rec.d2bytes = tl.d2bytes;
+      rec.hbytes = (int16_t)tl.hbytes;
+      rec.row0 = tl.row0;
+      rec.xrow0 = tl.xrow0;
+      rec.m = (int16_t)tl.m;
+      rec.rows = (int16_t)tl.rows;
+      if (l == last_leaf) {
+        rec.lleaf = (int16_t)(nl - 1);
+        continue;   // the leaf's level entries are in place
+      }
+      last_leaf = l;
+      rec.lleaf = (int16_t)nl++;
+      stlev.resize(stlev.size() + depth);
+      for (int k = 1; k <= depth; ++k) {
+        const int a = leaf_anc[l][k];
+        const int sib = node_index(k, (l >> (depth - k)) ^ 1);
+        const NodeDev& na = h->nodes[a];
+        StLev& e = stlev[stlev.size() - depth + (k - 1)];
+        memset(&e, 0, sizeof(e));
+        e.voff = leaf_vseg[l][k];
+        e.rV = (uint16_t)na.rV;
+        e.tierV = (uint8_t)na.tierV;
+        e.pslot = na.rV ? st_pslot0[a] + tile_slot[(size_t)t * depth + (k - 1)] * na.rV : -1;
+        const NodeDev& ns = h->nodes[sib];   // Y_sib multiplies U_a; rank rV(sib) = rU(a)
+        if (ns.rV == 0) {
+          e.yrow = -1;
+          continue;
+        }
+        auto it = yrow_of.find(sib);
+        if (it == yrow_of.end()) {
+          YItem y;
+          memset(&y, 0, sizeof(y));
+          y.pbase = st_pslot0[sib];
+          y.nslots = st_nslots[sib];
+          y.rV = ns.rV;
+          y.yrow = ycount;
+          y.invs = ns.invsV * na.invsU;
+          y.ntask = (y.nslots + kRedSlots - 1) / kRedSlots;
+          items.push_back(y);
+          it = yrow_of.emplace(sib, ycount).first;
+          ycount += ns.rV;
+        }
+        e.yrow = it->second;
+      }
+    }
+    sc.nl = nl;
+    st_max_leaves = std::max(st_max_leaves, nl);
+    // reduction tasks, the heaviest items first (warps take tasks in turn)
+    std::stable_sort(items.begin(), items.end(), [](const YItem& x, const YItem& y) {
+      return (int64_t)x.nslots * x.rV > (int64_t)y.nslots * y.rV;
+    });
+    int srow = 0;
+    sc.k0 = (int32_t)st_task.size();
+    for (size_t q = 0; q < items.size(); ++q) {
+      YItem& y = items[q];
+      y.srow = srow;
+      for (int p = 0; p < y.ntask; ++p) {
+        hodlr::RTask tk;
+        tk.yi = sc.y0 + (int)q;
+        tk.s0 = p * kRedSlots;
+        tk.s1 = std::min(y.nslots, (p + 1) * kRedSlots);
+        tk.srow = srow + p * y.rV;
+        st_task.push_back(tk);
+      }
+      srow += y.ntask * y.rV;
+    }
+    sc.nk = (int32_t)st_task.size() - sc.k0;
+    st_red_rows = std::max(st_red_rows, srow);
+    sc.ny = (int32_t)items.size();
+    st_y.insert(st_y.end(), items.begin(), items.end());
+    st_y_rows = std::max(st_y_rows, ycount);
+  }
+
   // ---- descriptors and scratch on the device ----
   hodlr_status st;
   if ((st = upload(h->nodes, &h->d_nodes)) != HODLR_OK) return st;
@@ -629,12 +884,22 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   if ((st = upload(h->vch_rest, &h->d_vch_rest)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
   if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
+  if (stlev.empty()) stlev.resize(1);   // depth 0: no level entries
+  if ((st = upload(stlev, &h->d_stlev)) != HODLR_OK) return st;
+  if ((st = upload(st_tile, &h->d_st_tile)) != HODLR_OK) return st;
+  if ((st = upload(st_cta, &h->d_st_cta)) != HODLR_OK) return st;
+  if ((st = upload(st_y, &h->d_st_y)) != HODLR_OK) return st;
+  if ((st = upload(st_task, &h->d_st_task)) != HODLR_OK) return st;
+  if ((st = upload(st_accoff, &h->d_st_accoff)) != HODLR_OK) return st;
   // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
   // for the rounded-up tile copies
   const size_t yb = ((size_t)std::max(yrows, 1) * h->max_nrhs + 4) * ebw;
   const size_t pb = (size_t)std::max(poff, 1) * h->max_nrhs * ebw;
   if (cudaMalloc(&h->d_Y, yb) != cudaSuccess) return fail(HODLR_ENOMEM, "Y scratch");
   if (cudaMalloc(&h->d_partials, pb) != cudaSuccess) return fail(HODLR_ENOMEM, "partials scratch");
+  // partial slots of the streamed product (batches of up to kStreamMaxCols columns)
+  const size_t spb = (size_t)std::max(st_p_rows, 1) * kStreamMaxCols * ebw;
+  if (cudaMalloc(&h->d_spart, spb) != cudaSuccess) return fail(HODLR_ENOMEM, "streamed partials scratch");
   // grid counter (starts at zero and only grows)
   const size_t sync_bytes = kSyncHeadBytes;
   if (cudaMalloc((void**)&h->d_sync, sync_bytes) != cudaSuccess) return fail(HODLR_ENOMEM, "grid counter");
@@ -644,7 +909,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
   CK(cudaMemsetAsync(h->d_Y, 0, yb, s));
   CK(cudaStreamSynchronize(s));
-  h->scratch_bytes = yb + pb + sync_bytes;
+  h->scratch_bytes = yb + pb + spb + sync_bytes;
 
   HandleDev& hd = h->hd;
   memset(&hd, 0, sizeof(hd));
@@ -685,12 +950,37 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     hd.leaf_m_max = std::max(hd.leaf_m_max, lf.m);
     if (lf.row0 % 4 || lf.m % 4) hd.x_aligned = 0;
   }
-  const int mb = matvec_max_batch(hd, h->work);
+  hd.stlev = h->d_stlev;
+  hd.st_tile = h->d_st_tile;
+  hd.st_max_leaves = st_max_leaves;
+  hd.st_cta = h->d_st_cta;
+  hd.st_y = h->d_st_y;
+  hd.st_task = h->d_st_task;
+  hd.st_accoff = h->d_st_accoff;
+  hd.st_grid = st_grid;
+  hd.st_p_rows = st_p_rows;
+  hd.st_y_rows = st_y_rows;
+  hd.st_acc_rows = st_acc_rows;
+  hd.st_max_rank = st_max_rank;
+  hd.st_red_rows = st_red_rows;
+  hd.st_max_tiles = st_max_tiles;
+  hd.st_max_vbytes = st_max_vbytes;
+  hd.st_max_cta_v = st_max_cta_v;
+  hd.st_max_cta_xrows = st_max_cta_xrows;
+  hd.st_max_tile_bytes = st_max_tile_bytes;
+  hd.st_max_cta_u = st_max_cta_u;
+  hd.st_max_ubytes = st_max_ubytes;
+  hd.st_max_d2bytes = st_max_d2bytes;
+  const int mb = std::min(matvec_max_batch(hd, h->work), stream_max_batch(hd, h->work));
   if (mb < 1) return fail(HODLR_EINVAL, "leaf blocks too large for the product's shared-memory stages; increase depth");
   h->batch = std::min(h->max_nrhs, mb);
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
                                h->leaves.size() * sizeof(LeafDev) + h->vch.size() * sizeof(VChunk) +
-                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + tcv.size() * sizeof(TcVRow) + h->vch_rest.size() * sizeof(VChunk) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t));
+                               h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + tcv.size() * sizeof(TcVRow) + h->vch_rest.size() * sizeof(VChunk) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t) +
+                               stlev.size() * sizeof(StLev) + st_y.size() * sizeof(YItem) +
+                               st_task.size() * sizeof(hodlr::RTask) + st_cta.size() * sizeof(hodlr::StCta) +
+                               st_tile.size() * sizeof(hodlr::StTile) +
+                               st_accoff.size() * sizeof(int32_t));
   return HODLR_OK;
 }
 
@@ -953,7 +1243,7 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
   const bool tc = h->work == HODLR_FP32 && nrhs >= kTcMinCols && h->hd.n_tcg_leaf > 0;
   // hodlr_debug_stall_next: the first launch of this call waits for grid
   // barrier arrivals that never come (the counter itself advances as usual)
-  unsigned long long skew = h->stall_next ? 4ull * matvec_sync_step(h->hd) : 0ull;
+  unsigned long long skew = h->stall_next ? 4ull * (matvec_sync_step(h->hd) + stream_sync_step(h->hd)) : 0ull;
   h->stall_next = false;
   const int step = tc ? std::min(h->max_nrhs, kTcMaxCols) : h->batch;
   for (int c0 = 0; c0 < nrhs; c0 += step) {
@@ -971,17 +1261,18 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
                         h->d_sync, h->sync_base + skew, s, nullptr, 1);
       skew = 0;
       if (ev) cudaEventRecord(ev[2], s);
+      h->sync_base += matvec_sync_step(h->hd);
     } else {
+      // CUDA cores: the streamed product in batches of h->batch columns
       for (int d0 = 0; d0 < nb && e == cudaSuccess; d0 += h->batch) {
         const int nd = std::min(h->batch, nb - d0);
         const bool lastd = d0 + h->batch >= nb;
-        e = launch_matvec(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_Y,
-                          h->d_partials, h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
+        e = launch_stream(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_spart,
+                          h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
         skew = 0;
-        if (!lastd) h->sync_base += matvec_sync_step(h->hd);
+        h->sync_base += stream_sync_step(h->hd);
       }
     }
-    h->sync_base += matvec_sync_step(h->hd);
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");
   }
   if (h->prof_on) h->prof_valid = true;

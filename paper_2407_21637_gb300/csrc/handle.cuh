@@ -18,6 +18,8 @@ using hodlr::TcGroup;
 using hodlr::TcVRow;
 using hodlr::PackTask;
 using hodlr::HandleDev;
+using hodlr::StLev;
+using hodlr::YItem;
 
 struct hodlr_s {
   std::vector<std::vector<std::pair<int, int>>> lv;  // cluster tree (row0, m) per level
@@ -33,6 +35,7 @@ struct hodlr_s {
   std::vector<NodeRed> nred;
   std::vector<P2Tile> p2;
   std::vector<PackTask> tasks;          // fp64 staging <-> pool, for export
+  std::vector<PackTask> tasks_v;        // fp64 staging -> V area of the tiles (packed, never unpacked)
   std::vector<int64_t> st_U, st_V, st_D; // staging offsets (elements)
   int64_t st_count = 0;
   hodlr_info_t info{};
@@ -51,6 +54,13 @@ struct hodlr_s {
   VChunk* d_vch_rest = nullptr;
   P2Tile* d_p2 = nullptr;
   int32_t* d_yscat = nullptr;
+  StLev* d_stlev = nullptr;               // streamed product: per (CTA, leaf, level)
+  hodlr::StTile* d_st_tile = nullptr;     // streamed product: per tile
+  hodlr::StCta* d_st_cta = nullptr;
+  YItem* d_st_y = nullptr;
+  hodlr::RTask* d_st_task = nullptr;
+  int32_t* d_st_accoff = nullptr;
+  void* d_spart = nullptr;                // its partial slots
   int* d_err = nullptr;
   void* d_Y = nullptr;
   void* d_partials = nullptr;
@@ -81,6 +91,13 @@ struct hodlr_s {
     cudaFree(d_vch_rest);
     cudaFree(d_p2);
     cudaFree(d_yscat);
+    cudaFree(d_stlev);
+    cudaFree(d_st_tile);
+    cudaFree(d_st_cta);
+    cudaFree(d_st_y);
+    cudaFree(d_st_task);
+    cudaFree(d_st_accoff);
+    cudaFree(d_spart);
     cudaFree(d_err);
     cudaFree(d_Y);
     cudaFree(d_partials);

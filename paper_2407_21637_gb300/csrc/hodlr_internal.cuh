@@ -85,24 +85,37 @@ struct NodeRed {
   int32_t pad_;
 };
 
-// Product tile: rows [t0, t0 + kTileRows) of a leaf.  Its data is one
-// contiguous region of the pool: a header of two words per level (byte
-// offset of the level's U block in the U area; rank | format << 16), the
-// ancestors' U rows for these 32 rows (level by level, column by column, 32
-// rows per column, each level in its own format), then the leaf block
-// D[t0:t0+32, :] row by row (row length m rounded up to 4, zero padded).
-// The D part streams through shared memory (it does not depend on V^T X);
-// header and U are read directly once Y is complete.
+// Product tile: rows [t0, t0 + kTileRows) of a leaf.  Its data sits in three
+// areas of the pool, each in tile order (so the parts of consecutive tiles
+// are contiguous):
+//  * U area: a header of two words per level (byte offset of the level's U
+//    block after the header; rank | format << 16), then the ancestors' U rows
+//    for these 32 rows (level by level, column by column, 32 rows per
+//    column, each level in its own format, each level 16-byte aligned);
+//  * D area: the leaf block D[t0:t0+32, :] row by row (row length m rounded
+//    up to 4, zero padded, working precision);
+//  * V area (streamed product): the ancestors' V rows for these 32 rows,
+//    laid out like the U rows (level by level, column by column, 32 rows per
+//    column, each level 16-byte aligned, in its format);
+//  * D2 area (streamed product): the leaf block D[t0:t0+32, :] once more,
+//    in chunks of 16 bytes per row (4 fp32 or 2 fp64 consecutive columns):
+//    chunk q of row r at (q * 32 + r) * 16, so that a warp with lane = row
+//    reads 512 contiguous bytes per chunk.
 struct P2Tile {
-  int64_t off;                    // byte offset of the region in the pool
-  int32_t bytes, hbytes, dbytes;  // region, header and D bytes (multiples of 16)
+  int64_t off;                    // byte offset of the header-and-U region in the pool
+  int64_t doff;                   // byte offset of the leaf-block part D[t0:t0+32, :] (128-byte aligned)
+  int64_t voff;                   // byte offset of the tile's V part (streamed product)
+  int64_t d2off;                  // byte offset of the tile's interleaved leaf-block part (streamed product)
+  int32_t d2bytes;                // bytes of the interleaved leaf-block part (multiple of 512)
+  int32_t vbytes;                 // bytes of the V part (multiple of 16)
+  int32_t bytes, hbytes, dbytes;  // header + U, header and D bytes (multiples of 16)
   int32_t m;                      // leaf rows = D columns
   int32_t rows;                   // valid rows in the tile (<= 32)
   int32_t row0;                   // first real row of the tile
   int32_t xrow0;                  // first real row of the leaf (row of X for column 0)
   int32_t nq;                     // U columns (sum of the ancestors' ranks)
   int32_t yrow;                   // first row of the leaf's block in the gathered Y
-  int32_t ubytes;                 // U bytes (multiple of 16); D starts at hbytes + ubytes
+  int32_t ubytes;                 // U bytes after the header (multiple of 16)
 };
 
 // Tensor-core products (fp32 work, many right-hand sides).  A leaf group is
@@ -130,6 +143,60 @@ struct TcVRow {
   int64_t off;                    // byte offset in the pool of the row's first element, or -1
   int32_t prow;                   // V group: partial row, or -1
   int32_t pad_;
+};
+
+// Streamed product (stream.cu).  Every CTA owns a contiguous range of
+// tiles, so of whole leaves except at its ends.  Per tile:
+struct StTile {
+  int64_t voff, uoff, d2off;      // pool byte offsets of the tile's V part, header + U region, D2 part
+  int32_t vbytes, ubytes, d2bytes;   // their bytes (ubytes includes the header)
+  int32_t row0, xrow0;            // first row of the tile and of its leaf
+  int16_t m, rows;                // leaf rows, tile rows
+  int16_t lleaf;                  // the tile's leaf among its CTA's leaves (0, 1, ...)
+  int16_t hbytes;                 // header bytes of the U region
+  int32_t pad_;
+};
+// Per (CTA, one of its leaves, level k = 1..depth), entry (l0 + leaf) *
+// depth + k - 1 (the same for every tile of the leaf in the CTA):
+struct StLev {
+  int32_t voff;                   // byte offset of the level's V block inside the tile's V part
+  int32_t pslot;                  // first partial row of (ancestor at level k, the tile's CTA), -1 if rank 0
+  int32_t yrow;                   // row in the CTA's Y area of Y of the ancestor's sibling, -1 if rank 0
+  uint16_t rV;                    // rank of V of the ancestor
+  uint8_t tierV, pad_;            // its storage format
+};
+// One Y_j a CTA needs for its U Y products: Y_j = invs * (sum of the
+// partial slots of node j), the slots of the CTAs that hold rows of j, in CTA
+// order.  The sum is split into tasks of at most kRedSlots slots whose
+// results go to the CTA's reduction scratch (rows srow + p * rV, task p),
+// then added in task order.
+constexpr int kRedSlots = 16;
+struct YItem {
+  int32_t pbase;                  // first partial row of the node's first slot
+  int32_t nslots;                 // number of slots
+  int32_t rV;                     // rows of Y_j
+  int32_t yrow;                   // first row in the CTA's Y area
+  double invs;                    // 1/s of V_j times 1/s of U of j's sibling
+  int32_t srow;                   // first row of its tasks' results in the reduction scratch
+  int32_t ntask;                  // ceil(nslots / kRedSlots)
+};
+// One reduction task: slots [s0, s1) of item yi (an index into st_y).
+struct RTask {
+  int32_t yi, s0, s1, srow;       // srow: first row of this task's result
+};
+// What one CTA of the streamed product owns.
+struct StCta {
+  int64_t voff;                   // first byte of its tiles' V parts (contiguous)
+  int64_t uoff;                   // first byte of its tiles' header + U regions (contiguous)
+  int32_t ubytes;                 // bytes of its tiles' header + U regions
+  int32_t pad0_;
+  int32_t t0, nt;                 // its tiles
+  int32_t l0, nl;                 // its leaves' level entries: st_lev rows (l0 .. l0 + nl) * depth
+  int32_t vbytes;                 // bytes of its tiles' V parts
+  int32_t xrow0, xrows;           // the rows of X its tiles cover
+  int32_t y0, ny;                 // its Y items (st_y)
+  int32_t k0, nk;                 // its reduction tasks (st_task)
+  int32_t pad_[3];
 };
 
 // Device-resident description of a handle (passed by value to kernels).
@@ -164,6 +231,28 @@ struct HandleDev {
   int32_t leaf_pm_max;
   int32_t leaf_m_max;             // largest leaf
   int32_t x_aligned;              // every leaf starts and ends on a multiple of 4 rows
+  // streamed product
+  const StTile* st_tile;          // [n_p2]
+  const StLev* stlev;             // level entries of every (CTA, leaf)
+  const StCta* st_cta;            // [st_grid]
+  const YItem* st_y;              // Y items of all CTAs
+  const RTask* st_task;           // reduction tasks of all CTAs
+  const int32_t* st_accoff;       // [depth + 1]: first accumulator row of level k
+  int32_t st_grid;                // CTAs of the launch (one per SM)
+  int32_t st_p_rows;              // rows of the partial buffer
+  int32_t st_y_rows;              // rows of the largest per-CTA Y area
+  int32_t st_red_rows;            // rows of the largest per-CTA reduction scratch
+  int32_t st_acc_rows;            // accumulator rows (sum over levels of the largest V rank)
+  int32_t st_max_rank;            // largest V rank
+  int32_t st_max_tiles;           // most tiles of one CTA
+  int32_t st_max_leaves;          // most leaves of one CTA
+  int32_t st_max_vbytes;          // largest V part of one tile
+  int32_t st_max_cta_v;           // largest V parts of one CTA (bytes) and
+  int32_t st_max_cta_xrows;       //   rows of X of one CTA
+  int32_t st_max_tile_bytes;      // largest header + U part plus leaf-block part of one tile
+  int32_t st_max_cta_u;           // largest header + U regions of one CTA (bytes)
+  int32_t st_max_ubytes;          // largest header + U region of one tile
+  int32_t st_max_d2bytes;         // largest interleaved leaf-block part of one tile
 };
 
 __host__ __device__ inline int node_index(int k, int i) { return (1 << k) - 2 + i; }
@@ -351,6 +440,19 @@ cudaError_t launch_matvec(const HandleDev& hd, int work, int nrhs, const void* X
 cudaError_t launch_leaf_tc(const TcGroup* groups, const int32_t* cta_first, int ncta, const TcVRow* vrows,
                            const uint8_t* pool, const float* X, int64_t ldx, int nrhs, float* B, int64_t ldb,
                            float* partials, int* err, cudaStream_t s);
+// The streamed product (stream.cu): one launch of nrhs <= kStreamMaxCols
+// right-hand sides, any working precision.  partials: st_p_rows * nrhs
+// values; sync: a grid counter whose value is sync_base when the launch
+// starts (the launch adds stream_sync_step).  ev as in launch_matvec.
+constexpr int kStreamMaxCols = 16;
+cudaError_t launch_stream(const HandleDev& hd, int work, int nrhs, const void* X, int64_t ldx, void* B,
+                          int64_t ldb, void* partials, unsigned long long* sync, unsigned long long sync_base,
+                          cudaStream_t s, cudaEvent_t* ev);
+unsigned long long stream_sync_step(const HandleDev& hd);
+// Widest batch launch_stream takes for this handle (0 when a single column
+// does not fit the shared memory).
+int stream_max_batch(const HandleDev& hd, int work);
+
 // The grid size launch_matvec uses.
 int matvec_grid(const HandleDev& hd);
 // How far one launch advances the grid barrier counter (sync_base of the
