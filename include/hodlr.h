@@ -206,9 +206,9 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
  * paper has no counterpart; this is a library convenience.
  *
  * It allocates nothing (no cudaMalloc, cudaFree or allocating library call)
- * and does not use the handle's own scratch: its scratch is one 1 MiB device
- * array inside this library, which every GPU that loads the library holds
- * until the process exits.  Arguments and results are those of
+ * and does not use the handle's own scratch: its scratch is one 256 KiB
+ * device array inside this library, which every GPU that loads the library
+ * holds until the process exits.  Arguments and results are those of
  * hodlr_matvec.  It always runs the CUDA-core product, in batches of columns
  * that fit the array (at most as many as hodlr_matvec takes per launch).
  * Where hodlr_matvec takes the CUDA-core path with the same batches (fp64
@@ -216,9 +216,11 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
  * batch, B is bitwise the same; fp32 products of 16 or more columns, which
  * hodlr_matvec runs on the tensor cores, and products split into narrower
  * batches agree within the rounding bound of the products.  A matrix whose
- * per-column scratch (its partial V^T X sums: about one value per rank
- * column, per node and per SM that holds rows of the node) does not fit at
- * all is rejected with HODLR_EINVAL before anything is enqueued.
+ * per-column scratch (its partial V^T X sums: one value per rank column, per
+ * node and per SM that holds rows of the node) does not fit at all, or
+ * whose ranks are too large for the streamed product's shared-memory stages
+ * (hodlr_matvec then takes its other CUDA-core kernel), is rejected with
+ * HODLR_EINVAL before anything is enqueued.
  *
  * The current device must be the handle's device (HODLR_EINVAL otherwise):
  * the array's device address is looked up on the current device on every

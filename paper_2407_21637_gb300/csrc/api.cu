@@ -971,7 +971,12 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   hd.st_max_cta_u = st_max_cta_u;
   hd.st_max_ubytes = st_max_ubytes;
   hd.st_max_d2bytes = st_max_d2bytes;
-  const int mb = std::min(matvec_max_batch(hd, h->work), stream_max_batch(hd, h->work));
+  // CUDA-core products: the streamed kernel when its shared-memory plan fits
+  // (every realistic rank), else the two-barrier kernel, which reads U rows
+  // that do not fit from global memory
+  const int sb = stream_max_batch(hd, h->work);
+  h->use_stream = sb > 0;
+  const int mb = h->use_stream ? sb : matvec_max_batch(hd, h->work);
   if (mb < 1) return fail(HODLR_EINVAL, "leaf blocks too large for the product's shared-memory stages; increase depth");
   h->batch = std::min(h->max_nrhs, mb);
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
@@ -1267,10 +1272,16 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
       for (int d0 = 0; d0 < nb && e == cudaSuccess; d0 += h->batch) {
         const int nd = std::min(h->batch, nb - d0);
         const bool lastd = d0 + h->batch >= nb;
-        e = launch_stream(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_spart,
-                          h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
+        if (h->use_stream) {
+          e = launch_stream(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_spart,
+                            h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
+          h->sync_base += stream_sync_step(h->hd);
+        } else {
+          e = launch_matvec(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_Y,
+                            h->d_partials, h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
+          h->sync_base += matvec_sync_step(h->hd);
+        }
         skew = 0;
-        h->sync_base += stream_sync_step(h->hd);
       }
     }
     if (e != cudaSuccess) return cuda_fail(e, "hodlr_matvec launch");

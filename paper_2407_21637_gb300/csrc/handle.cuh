@@ -25,6 +25,7 @@ struct hodlr_s {
   std::vector<std::vector<std::pair<int, int>>> lv;  // cluster tree (row0, m) per level
   int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
   int batch = 64;                      // right-hand sides per product launch
+  bool use_stream = true;              // CUDA-core products by the streamed kernel (else the two-barrier one)
   double eps = 0.0;
   uint32_t avail = 0;
   int device = 0;

@@ -21,7 +21,7 @@
 namespace hodlr {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;   // 1 MiB per device
+constexpr size_t kNoAllocScratchBytes = size_t(256) << 10;   // 256 KiB per device
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -54,7 +54,10 @@ extern "C" hodlr_status hodlr_matvec_noalloc(hodlr_t h, int32_t nrhs, const void
   const size_t counter_bytes = kSyncHeadBytes;
   const size_t per_col = (size_t)std::max(h->hd.st_p_rows, 1) * es;
   if (counter_bytes + per_col > kNoAllocScratchBytes)
-    return set_error(HODLR_EINVAL, "matrix too large for the 1 MiB static scratch of hodlr_matvec_noalloc "
+    return set_error(HODLR_EINVAL, "matrix too large for the 256 KiB static scratch of hodlr_matvec_noalloc "
+                                   "(use hodlr_matvec)");
+  if (!h->use_stream)
+    return set_error(HODLR_EINVAL, "ranks too large for the streamed product that hodlr_matvec_noalloc runs "
                                    "(use hodlr_matvec)");
   const int nb_max = (int)std::min<size_t>(std::min<size_t>((size_t)nrhs, (size_t)h->batch),
                                            (kNoAllocScratchBytes - counter_bytes) / per_col);
