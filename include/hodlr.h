@@ -211,11 +211,12 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx,
  * holds until the process exits.  Arguments and results are those of
  * hodlr_matvec.  It always runs the CUDA-core product, in batches of columns
  * that fit the array (at most as many as hodlr_matvec takes per launch).
- * Where hodlr_matvec takes the CUDA-core path with the same batches (fp64
- * work; fp32 work with fewer than 16 columns) and the array holds a whole
- * batch, B is bitwise the same; fp32 products of 16 or more columns, which
- * hodlr_matvec runs on the tensor cores, and products split into narrower
- * batches agree within the rounding bound of the products.  A matrix whose
+ * Where hodlr_matvec runs the same kernel with the same batches (fp32 work
+ * with fewer than 16 columns, fp64 work with one column) and the array
+ * holds a whole batch, B is bitwise the same; other products (fp32 with 16
+ * or more columns, which hodlr_matvec runs on the tensor cores, fp64 with
+ * more columns, which it runs on its two-barrier kernel, and products split
+ * into narrower batches) agree within the rounding bound of the products.  A matrix whose
  * per-column scratch (its partial V^T X sums: one value per rank column, per
  * node and per SM that holds rows of the node) does not fit at all, or
  * whose ranks are too large for the streamed product's shared-memory stages

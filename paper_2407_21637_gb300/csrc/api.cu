@@ -1272,7 +1272,9 @@ hodlr_status hodlr_matvec(hodlr_t h, int32_t nrhs, const void* X, int64_t ldx, v
       for (int d0 = 0; d0 < nb && e == cudaSuccess; d0 += h->batch) {
         const int nd = std::min(h->batch, nb - d0);
         const bool lastd = d0 + h->batch >= nb;
-        if (h->use_stream) {
+        // fp64 work is bound by the FP64 multiply-add rate; beyond one column
+        // the two-barrier kernel's lane layouts use it better
+        if (h->use_stream && (h->work != HODLR_FP64 || nd == 1)) {
           e = launch_stream(h->hd, h->work, nd, xb + (c0 + d0) * es, ldx, bb + (c0 + d0) * es, ldb, h->d_spart,
                             h->d_sync, h->sync_base + skew, s, lastd ? ev : nullptr);
           h->sync_base += stream_sync_step(h->hd);

@@ -1,8 +1,10 @@
 """Parity at the benchmark's full size, in the launch configuration bench.py
 times: gauss_65536 (n = 65536 sorted U[0,1] points, exp(-r^2/0.01) + 1e-2 I,
-leaf 256, depth 8, eps 1e-6, fp32 work, formats {fp64, fp32, bf16, fp16,
-e4m3}) built on the GPU with max_nrhs 64, products of R = 1, 8 and 64
-columns (CUDA cores; CUDA cores with four columns per lane; tensor cores).
+leaf 256, depth 8, eps 1e-6, per-block rule over {fp64, fp32, bf16, fp16,
+e4m3}, fp32 work) and the benchmark's mixed-format workload on the same
+points (1/(|x_i - x_j| + 1e-3), eps 1e-4, per-block rule: fp32 and fp16
+blocks), both built on the GPU with max_nrhs 64, products of R = 1, 8 and 64
+columns (streamed CUDA-core kernel; tensor cores from 16 columns on).
 The oracle's fp64 product of the same stored generators (exported exactly)
 is formed on sampled rows -- both ends of every leaf, the matrix ends and
 seeded random rows -- and every sampled entry must lie within the
@@ -23,17 +25,20 @@ from oracle.abi_lists import abi_to_levels
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def full():
+@pytest.fixture(scope="module", params=["headline", "mixed"])
+def full(request):
     from paper_2407_21637_gb300 import build as B
     from paper_2407_21637_gb300 import HodlrMatrix
     B.build()
     torch.cuda.set_device(0)
-    W = bench.WL
+    W = bench.WL if request.param == "headline" else bench.WL_MIXED
     n, depth = W["n"], W["depth"]
     pts = torch.from_numpy(synth.uniform_points_1d(n, W["seed"])).cuda()
     g = HodlrMatrix.build(pts, W["kind"], depth, W["eps"], c=W["c"], len2=W["len2"], diag=W["diag"],
-                          work=W["work"], tiers=W["tiers"], max_nrhs=64)
+                          work=W["work"], tiers=W["tiers"], per_block=W["per_block"], max_nrhs=64)
+    if request.param == "mixed":   # the adaptive rule must really have mixed formats here
+        bpt = g.info()["bytes_per_tier"]
+        assert bpt["fp16"] > 0 and bpt["fp32"] > 0
     U, V, D = g.export()
     h = C.from_factors(n, depth, abi_to_levels(depth, U), abi_to_levels(depth, V), D)
     h.Uh, h.Vh, h.Dh = h.U, h.V, h.D          # the exported values are the stored ones
