@@ -849,7 +849,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       y.srow = srow;
       for (int p = 0; p < y.ntask; ++p) {
         hodlr::RTask tk;
-        tk.yi = sc.y0 + (int)q;
+        tk.yi = (int)q;   // the CTA's q-th Y item
         tk.s0 = p * kRedSlots;
         tk.s1 = std::min(y.nslots, (p + 1) * kRedSlots);
         tk.srow = srow + p * y.rV;
@@ -884,13 +884,32 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   if ((st = upload(h->vch_rest, &h->d_vch_rest)) != HODLR_OK) return st;
   if ((st = upload(h->p2, &h->d_p2)) != HODLR_OK) return st;
   if ((st = upload(yscat, &h->d_yscat)) != HODLR_OK) return st;
-  if (stlev.empty()) stlev.resize(1);   // depth 0: no level entries
-  if ((st = upload(stlev, &h->d_stlev)) != HODLR_OK) return st;
-  if ((st = upload(st_tile, &h->d_st_tile)) != HODLR_OK) return st;
-  if ((st = upload(st_cta, &h->d_st_cta)) != HODLR_OK) return st;
-  if ((st = upload(st_y, &h->d_st_y)) != HODLR_OK) return st;
-  if ((st = upload(st_task, &h->d_st_task)) != HODLR_OK) return st;
-  if ((st = upload(st_accoff, &h->d_st_accoff)) != HODLR_OK) return st;
+  // one fixed-size record per CTA of the streamed product (StCta): its
+  // header, tiles, level entries, accumulator offsets, tasks and Y items
+  int st_max_nk = 0, st_max_ny = 0;
+  for (const hodlr::StCta& sc : st_cta) {
+    st_max_nk = std::max(st_max_nk, sc.nk);
+    st_max_ny = std::max(st_max_ny, sc.ny);
+  }
+  const int dl = std::max(depth, 1);
+  const int off_tile = (int)align_up(sizeof(hodlr::StCta), 16);
+  const int off_lev = off_tile + (int)align_up((size_t)st_max_tiles * sizeof(hodlr::StTile), 16);
+  const int off_acc = off_lev + (int)align_up((size_t)st_max_leaves * dl * sizeof(StLev), 16);
+  const int off_task = off_acc + (int)align_up((size_t)(depth + 1) * sizeof(int32_t), 16);
+  const int off_y = off_task + (int)align_up((size_t)st_max_nk * sizeof(hodlr::RTask), 16);
+  const int blob_stride = (int)align_up((size_t)off_y + (size_t)st_max_ny * sizeof(YItem), 16);
+  std::vector<uint8_t> blob((size_t)blob_stride * st_grid, 0);
+  for (int c = 0; c < st_grid; ++c) {
+    const hodlr::StCta& sc = st_cta[c];
+    uint8_t* b = blob.data() + (size_t)c * blob_stride;
+    memcpy(b, &sc, sizeof(sc));
+    if (sc.nt) memcpy(b + off_tile, &st_tile[sc.t0], sizeof(hodlr::StTile) * sc.nt);
+    if (sc.nl && depth) memcpy(b + off_lev, &stlev[(size_t)sc.l0 * depth], sizeof(StLev) * sc.nl * depth);
+    memcpy(b + off_acc, st_accoff.data(), sizeof(int32_t) * (depth + 1));
+    if (sc.nk) memcpy(b + off_task, &st_task[sc.k0], sizeof(hodlr::RTask) * sc.nk);
+    if (sc.ny) memcpy(b + off_y, &st_y[sc.y0], sizeof(YItem) * sc.ny);
+  }
+  if ((st = upload(blob, &h->d_st_blob)) != HODLR_OK) return st;
   // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
   // for the rounded-up tile copies
   const size_t yb = ((size_t)std::max(yrows, 1) * h->max_nrhs + 4) * ebw;
@@ -950,13 +969,14 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     hd.leaf_m_max = std::max(hd.leaf_m_max, lf.m);
     if (lf.row0 % 4 || lf.m % 4) hd.x_aligned = 0;
   }
-  hd.stlev = h->d_stlev;
-  hd.st_tile = h->d_st_tile;
+  hd.st_blob = h->d_st_blob;
+  hd.st_blob_stride = blob_stride;
+  hd.st_off_tile = off_tile;
+  hd.st_off_lev = off_lev;
+  hd.st_off_acc = off_acc;
+  hd.st_off_task = off_task;
+  hd.st_off_y = off_y;
   hd.st_max_leaves = st_max_leaves;
-  hd.st_cta = h->d_st_cta;
-  hd.st_y = h->d_st_y;
-  hd.st_task = h->d_st_task;
-  hd.st_accoff = h->d_st_accoff;
   hd.st_grid = st_grid;
   hd.st_p_rows = st_p_rows;
   hd.st_y_rows = st_y_rows;
@@ -982,10 +1002,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   inf.device_bytes = (int64_t)(pool + h->scratch_bytes + h->nodes.size() * sizeof(NodeDev) +
                                h->leaves.size() * sizeof(LeafDev) + h->vch.size() * sizeof(VChunk) +
                                h->nred.size() * sizeof(NodeRed) + ritems.size() * sizeof(int2) + tcg.size() * sizeof(TcGroup) + tcv.size() * sizeof(TcVRow) + h->vch_rest.size() * sizeof(VChunk) + h->p2.size() * sizeof(P2Tile) + yscat.size() * sizeof(int32_t) +
-                               stlev.size() * sizeof(StLev) + st_y.size() * sizeof(YItem) +
-                               st_task.size() * sizeof(hodlr::RTask) + st_cta.size() * sizeof(hodlr::StCta) +
-                               st_tile.size() * sizeof(hodlr::StTile) +
-                               st_accoff.size() * sizeof(int32_t));
+                               blob.size());
   return HODLR_OK;
 }
 

@@ -55,12 +55,7 @@ struct hodlr_s {
   VChunk* d_vch_rest = nullptr;
   P2Tile* d_p2 = nullptr;
   int32_t* d_yscat = nullptr;
-  StLev* d_stlev = nullptr;               // streamed product: per (CTA, leaf, level)
-  hodlr::StTile* d_st_tile = nullptr;     // streamed product: per tile
-  hodlr::StCta* d_st_cta = nullptr;
-  YItem* d_st_y = nullptr;
-  hodlr::RTask* d_st_task = nullptr;
-  int32_t* d_st_accoff = nullptr;
+  uint8_t* d_st_blob = nullptr;           // streamed product: one record per CTA
   void* d_spart = nullptr;                // its partial slots
   int* d_err = nullptr;
   void* d_Y = nullptr;
@@ -92,12 +87,7 @@ struct hodlr_s {
     cudaFree(d_vch_rest);
     cudaFree(d_p2);
     cudaFree(d_yscat);
-    cudaFree(d_stlev);
-    cudaFree(d_st_tile);
-    cudaFree(d_st_cta);
-    cudaFree(d_st_y);
-    cudaFree(d_st_task);
-    cudaFree(d_st_accoff);
+    cudaFree(d_st_blob);
     cudaFree(d_spart);
     cudaFree(d_err);
     cudaFree(d_Y);

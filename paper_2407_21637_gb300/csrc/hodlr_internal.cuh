@@ -180,22 +180,28 @@ struct YItem {
   int32_t srow;                   // first row of its tasks' results in the reduction scratch
   int32_t ntask;                  // ceil(nslots / kRedSlots)
 };
-// One reduction task: slots [s0, s1) of item yi (an index into st_y).
+// One reduction task: slots [s0, s1) of item yi (the CTA's yi-th Y item).
 struct RTask {
   int32_t yi, s0, s1, srow;       // srow: first row of this task's result
 };
-// What one CTA of the streamed product owns.
+// What one CTA of the streamed product owns.  Everything a CTA reads about
+// its own work is one record of fixed size (st_blob_stride bytes) that the
+// CTA fetches with one bulk copy at the start: this header, then its tiles
+// (StTile[nt] at st_off_tile), its leaves' level entries (StLev[nl * depth]
+// at st_off_lev), the accumulator offsets (int32[depth + 1] at st_off_acc),
+// its reduction tasks (RTask[nk] at st_off_task) and its Y items (YItem[ny]
+// at st_off_y).
 struct StCta {
   int64_t voff;                   // first byte of its tiles' V parts (contiguous)
   int64_t uoff;                   // first byte of its tiles' header + U regions (contiguous)
   int32_t ubytes;                 // bytes of its tiles' header + U regions
   int32_t pad0_;
   int32_t t0, nt;                 // its tiles
-  int32_t l0, nl;                 // its leaves' level entries: st_lev rows (l0 .. l0 + nl) * depth
+  int32_t l0, nl;                 // its leaves
   int32_t vbytes;                 // bytes of its tiles' V parts
   int32_t xrow0, xrows;           // the rows of X its tiles cover
-  int32_t y0, ny;                 // its Y items (st_y)
-  int32_t k0, nk;                 // its reduction tasks (st_task)
+  int32_t y0, ny;                 // its Y items
+  int32_t k0, nk;                 // its reduction tasks
   int32_t pad_[3];
 };
 
@@ -232,12 +238,9 @@ struct HandleDev {
   int32_t leaf_m_max;             // largest leaf
   int32_t x_aligned;              // every leaf starts and ends on a multiple of 4 rows
   // streamed product
-  const StTile* st_tile;          // [n_p2]
-  const StLev* stlev;             // level entries of every (CTA, leaf)
-  const StCta* st_cta;            // [st_grid]
-  const YItem* st_y;              // Y items of all CTAs
-  const RTask* st_task;           // reduction tasks of all CTAs
-  const int32_t* st_accoff;       // [depth + 1]: first accumulator row of level k
+  const uint8_t* st_blob;         // [st_grid] records of st_blob_stride bytes (see StCta)
+  int32_t st_blob_stride;         // bytes per record (a multiple of 16)
+  int32_t st_off_tile, st_off_lev, st_off_acc, st_off_task, st_off_y;   // sections of a record
   int32_t st_grid;                // CTAs of the launch (one per SM)
   int32_t st_p_rows;              // rows of the partial buffer
   int32_t st_y_rows;              // rows of the largest per-CTA Y area

@@ -49,14 +49,17 @@ constexpr int kSThreads = 32 * kSWarps;
 constexpr int kSAll = kSThreads + 32;                 // consumers and the producer warp
 constexpr int kSStagesMax = 8;
 constexpr int kSXMax = 32 * 1024;                     // a leaf's X rows staged with its tiles up to this
+constexpr int kSInflight = 2;                         // leaf-block copies in flight per CTA at most
 
 // Shared-memory plan of one launch (host computed).
 struct SPlan {
   int nstages, stage_bytes;                // the leaf-block ring
-  int nvw;                                 // V warps (V phase, reduction); the other consumers are D warps
+  int dmax;                                // leaf-block copies in flight at most
+  int nvw;                                 // V warps (V phase, reduction, U Y); the other consumers are D warps
   int wps;                                 // D warps per ring stage (one group per stage)
   int vu_off, vu_bytes;                    // the V/U area
   int res_off, res_smem;                   // D X results of the CTA's tiles (in shared memory when they fit)
+  int uy_off, uy_smem;                     // U Y of the CTA's tiles (computed by the V warps when it fits)
   int part_off;                            // partial rows of the D groups' helpers
   int acc_off, ys_off, red_off, bar_off, meta_off;   // byte offsets in dynamic shared memory
   int xstaged;                             // X rows travel with the copies
@@ -137,12 +140,16 @@ struct SLanes {
 
 __host__ __device__ __forceinline__ int al16(int x) { return (x + 15) & ~15; }
 
-__device__ __forceinline__ void bar_v(int nvw) { asm volatile("bar.sync 1, %0;" ::"r"(32 * nvw) : "memory"); }
-__device__ __forceinline__ void bar_cons() { asm volatile("bar.sync 2, %0;" ::"r"(kSThreads) : "memory"); }
-// Barrier of the warps of D group g (nthreads threads) that also returns
-// whether p held on every one of them, so that a wait that gave up in one
-// warp stops the whole group at the same tile.
-__device__ __forceinline__ bool group_all(int g, bool p, int nthreads) {
+// Named barriers: 0 is __syncthreads, then the V warps, all consumers,
+// the D groups (one per ring stage) and two votes.
+constexpr int kBarV = 1, kBarCons = 2, kBarGroup0 = 3, kBarVote = kBarGroup0 + kSStagesMax, kBarConsVote = kBarVote + 1;
+static_assert(kBarConsVote < 16, "16 named barriers per CTA");
+__device__ __forceinline__ void bar_v(int nvw) { asm volatile("bar.sync %0, %1;" ::"r"(kBarV), "r"(32 * nvw) : "memory"); }
+__device__ __forceinline__ void bar_cons() { asm volatile("bar.sync %0, %1;" ::"r"(kBarCons), "r"(kSThreads) : "memory"); }
+// Barrier id of nthreads threads that also returns whether p held on every
+// one of them, so that a wait that gave up in one warp stops them all at the
+// same point.
+__device__ __forceinline__ bool bar_and(int id, bool p, int nthreads) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred pi, po;\n\t"
@@ -150,7 +157,7 @@ __device__ __forceinline__ bool group_all(int g, bool p, int nthreads) {
       "bar.red.and.pred po, %2, %3, pi;\n\t"
       "selp.u32 %0, 1, 0, po;\n\t}"
       : "=r"(r)
-      : "r"((uint32_t)p), "r"(3 + g), "r"(nthreads)
+      : "r"((uint32_t)p), "r"(id), "r"(nthreads)
       : "memory");
   return r != 0;
 }
@@ -202,6 +209,61 @@ __device__ __forceinline__ void copy_u_chunk(const HandleDev& hd, const StTile* 
   if (ub) bulk_g2s(area, hd.pool + u0, (uint32_t)ub, bar);
 }
 
+// B rows of one tile += sum over levels of U_{a_k}[rows, :] Y_{a_k ^ 1}: the
+// tile's header and U columns at st (column-major, 32 rows per column),
+// lane = row, Y rows broadcast from the CTA's Y area (read BW values wide:
+// values past R are never stored).
+template <typename W, int BW>
+__device__ __forceinline__ void tile_uy(const uint8_t* st, int hbytes, const StLev* lev, int depth, const W* ys_s,
+                                        int R, int r, bool xvec, W (&acc)[BW]) {
+  for (int k = 1; k <= depth; ++k) {
+    const uint2 hw = reinterpret_cast<const uint2*>(st)[k - 1];
+    const uint32_t w0 = hw.x, w1 = hw.y;
+    const int ru = (int)(w1 & 0xffffu), tier = (int)(w1 >> 16);
+    if (ru == 0) continue;
+    const W* const yb = ys_s + lev[k - 1].yrow * R;
+    auto level = [&](auto tc) {
+      constexpr int TIER = decltype(tc)::value;
+      constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+      const uint8_t* const ucol = st + hbytes + w0 + r * eb;
+      if (xvec) {
+#pragma unroll 4
+        for (int c = 0; c < ru; ++c) {
+          const W u = ldf<W, TIER>(ucol + c * kTileRows * eb);
+          W yv[BW];
+          ld_row<W, BW, true>(yb + c * R, yv);
+#pragma unroll
+          for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
+        }
+      } else {
+#pragma unroll 4
+        for (int c = 0; c < ru; ++c) {
+          const W u = ldf<W, TIER>(ucol + c * kTileRows * eb);
+          W yv[BW];
+          ld_row<W, BW, false>(yb + c * R, yv);
+#pragma unroll
+          for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
+        }
+      }
+    };
+    with_format(tier, level);
+  }
+}
+
+// B row r of a tile (tile rows only), as 16-byte vectors where aligned
+template <typename W, int BW>
+__device__ __forceinline__ void store_brow(W* brow, int R, bool xvec, int64_t ldb, const W (&acc)[BW]) {
+  if (xvec && ldb % 4 == 0 && (reinterpret_cast<uintptr_t>(brow) & 15) == 0) {
+#pragma unroll
+    for (int j4 = 0; j4 < BW / 4; ++j4)
+      *reinterpret_cast<float4*>(brow + 4 * j4) = make_float4(acc[4 * j4], acc[4 * j4 + 1], acc[4 * j4 + 2], acc[4 * j4 + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < BW; ++j)
+      if (j < R) brow[j] = acc[j];
+  }
+}
+
 template <typename W, int LC, int CPL>
 __global__ void __launch_bounds__(kSAll, 1)
 stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W* __restrict__ part,
@@ -217,17 +279,15 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   uint64_t* empty = full + kSStagesMax;
   uint64_t* vfull = empty + kSStagesMax;       // a V chunk has landed in the V/U area
   uint64_t* ufull = vfull + 1;                 // a U chunk has landed in the V/U area
-  int* s_ok = reinterpret_cast<int*>(ufull + 1);   // the grid counter was reached
+  uint64_t* mfull = ufull + 1;                 // the CTA's record has landed
+  int* s_ok = reinterpret_cast<int*>(mfull + 1);   // the grid counter was reached
   const int G = gridDim.x;
-  const StCta cta = hd.st_cta[blockIdx.x];
-  const int nt = cta.nt;
   const int depth = hd.depth;
-  const int xrow_bytes = pl.xstaged ? R * es : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
   uint8_t* const vu = smem + pl.vu_off;
   const int vcap = pl.vu_bytes;
-  // the whole V range of this CTA in one chunk, copied before anything else
-  const bool v_one = depth > 0 && nt > 0 && al16(cta.vbytes) + cta.xrows * xrow_bytes <= vcap;
+  uint8_t* const meta = smem + pl.meta_off;
+  // the CTA's record (StCta and its sections), one bulk copy before anything else
   if (warp == kSWarps && lane == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -235,36 +295,30 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     }
     mbar_init(vfull, 1);
     mbar_init(ufull, 1);
+    mbar_init(mfull, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if (v_one) {
-      const int xb = cta.xrows * xrow_bytes;
-      mbar_arrive_expect_tx(vfull, (uint32_t)(cta.vbytes + xb));
-      if (cta.vbytes) bulk_g2s(vu, hd.pool + cta.voff, (uint32_t)cta.vbytes, vfull);
-      if (xb) bulk_g2s(vu + al16(cta.vbytes), X + (int64_t)cta.xrow0 * R, (uint32_t)xb, vfull);
+    mbar_arrive_expect_tx(mfull, (uint32_t)hd.st_blob_stride);
+    bulk_g2s(meta, hd.st_blob + (size_t)blockIdx.x * hd.st_blob_stride, (uint32_t)hd.st_blob_stride, mfull);
+  }
+  __syncthreads();
+  {
+    const bool ok = mbar_wait(mfull, 0, hd.err, 7);
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      // a wait gave up: let the copy land (bounded) before the CTA exits
+      if (warp == kSWarps && lane == 0) mbar_wait(mfull, 0, hd.err, 7);
+      return;
     }
   }
-  // This CTA's tile records (tiles[j] = tile t0 + j), the level entries of
-  // its leaves (llev[leaf * depth + k - 1]) and the accumulator offsets,
-  // copied to shared memory once (every role reads them many times; taken
-  // from the shared-memory array, the reads are shared-memory loads).
-  StTile* const tiles = reinterpret_cast<StTile*>(smem + pl.meta_off);
-  StLev* const llev = reinterpret_cast<StLev*>(smem + pl.meta_off + al16(hd.st_max_tiles * (int)sizeof(StTile)));
-  int32_t* const accoff = reinterpret_cast<int32_t*>(
-      reinterpret_cast<uint8_t*>(llev) + al16(hd.st_max_leaves * (depth > 0 ? depth : 1) * (int)sizeof(StLev)));
-  {
-    const int nw = nt * (int)(sizeof(StTile) / 8);
-    const uint2* src = reinterpret_cast<const uint2*>(hd.st_tile + cta.t0);
-    uint2* dst = reinterpret_cast<uint2*>(tiles);
-    for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = __ldg(src + w);
-  }
-  {
-    const int nw = cta.nl * depth * (int)(sizeof(StLev) / 16);
-    const uint4* src = reinterpret_cast<const uint4*>(hd.stlev + (size_t)cta.l0 * depth);
-    uint4* dst = reinterpret_cast<uint4*>(llev);
-    for (int w = threadIdx.x; w < nw; w += blockDim.x) dst[w] = __ldg(src + w);
-  }
-  for (int w = threadIdx.x; w <= depth; w += blockDim.x) accoff[w] = __ldg(hd.st_accoff + w);
-  __syncthreads();
+  const StCta& cta = *reinterpret_cast<const StCta*>(meta);
+  const StTile* const tiles = reinterpret_cast<const StTile*>(meta + hd.st_off_tile);
+  const StLev* const llev = reinterpret_cast<const StLev*>(meta + hd.st_off_lev);
+  const int32_t* const accoff = reinterpret_cast<const int32_t*>(meta + hd.st_off_acc);
+  const RTask* const tasks = reinterpret_cast<const RTask*>(meta + hd.st_off_task);
+  const YItem* const yitems = reinterpret_cast<const YItem*>(meta + hd.st_off_y);
+  const int nt = cta.nt;
+  const int xrow_bytes = pl.xstaged ? R * es : 0;
+  // the whole V range of this CTA in one chunk when it fits
+  const bool v_one = depth > 0 && nt > 0 && al16(cta.vbytes) + cta.xrows * xrow_bytes <= vcap;
 
   // chunks of the V phase and of the U phase (every role takes the same)
   int nvch = 0, nuch = 0;
@@ -274,17 +328,29 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     for (int t = 0; t < nt; ++nuch) t = next_u_chunk(tiles, t, nt, vcap);
 
   if (warp == kSWarps) {
-    // ================= producer: the leaf-block ring =================
+    // ================= producer =================
     if (lane != 0) return;
+    // the V bytes first (the V phase, the grid counter and the reduction are
+    // the launch's critical path), then the leaf blocks through the ring,
+    // at most pl.dmax copies in flight: a longer queue of leaf-block bytes
+    // adds its drain time to every critical-path access of this SM
+    if (v_one) {
+      const int xb = cta.xrows * xrow_bytes;
+      mbar_arrive_expect_tx(vfull, (uint32_t)(cta.vbytes + xb));
+      if (cta.vbytes) bulk_g2s(vu, hd.pool + cta.voff, (uint32_t)cta.vbytes, vfull);
+      if (xb) bulk_g2s(vu + al16(cta.vbytes), X + (int64_t)cta.xrow0 * R, (uint32_t)xb, vfull);
+    } else if (nvch > 0) {
+      copy_v_chunk(hd, tiles, 0, next_v_chunk(tiles, 0, nt, vcap, xrow_bytes), X, R, xrow_bytes, vu, vfull);
+    }
+    // (a cap of S or more is the ring's own: copy j - S has been consumed,
+    // and the phase of an older copy may already have been reused)
+    const int DM = max(pl.dmax, 1);
     bool ok = true;
-    if (nvch > 0 && !v_one) copy_v_chunk(hd, tiles, 0, next_v_chunk(tiles, 0, nt, vcap, xrow_bytes), X, R, xrow_bytes, vu, vfull);
-    // the V bytes first: the V phase, the grid counter and the reduction are
-    // the launch's critical path, the leaf blocks have slack
-    if (nvch > 0) ok = mbar_wait(vfull, 0, hd.err, 1);
     int j = 0;
     for (; j < nt && ok; ++j) {
       const int s = j % S;
       if (j >= S && !(ok = mbar_wait(&empty[s], ((j / S) - 1) & 1, hd.err, 1))) break;
+      if (DM < S && j >= DM && !(ok = mbar_wait(&full[(j - DM) % S], ((j - DM) / S) & 1, hd.err, 1))) break;
       const StTile& q = tiles[j];
       const int db = q.d2bytes, xb = q.m * xrow_bytes;
       uint8_t* st = smem + (size_t)s * SB;
@@ -303,6 +369,8 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   W* const ys_s = reinterpret_cast<W*>(smem + pl.ys_off);
   W* const red_s = reinterpret_cast<W*>(smem + pl.red_off);
   W* const res_s = reinterpret_cast<W*>(smem + pl.res_off);
+  W* const uy_s = reinterpret_cast<W*>(smem + pl.uy_off);
+  const bool xvec = sizeof(W) == 4 && BW % 4 == 0 && R % 4 == 0;
   bool alive = true;
 
   if (warp < NVW) {
@@ -444,19 +512,20 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     // ---- reduction: once every CTA has arrived, the Y this CTA needs.
     //      Tasks of up to kRedSlots slots (one round of loads per lane),
     //      then the tasks of every item added in order ----
+    bool red_ok = true;
     if (cta.ny > 0) {
       if (tid == 0) *s_ok = grid_wait(sync, sync_base + (unsigned long long)G, hd.err) ? 1 : 0;
       bar_v(NVW);
-      const bool red_ok = *s_ok != 0;
+      red_ok = *s_ok != 0;
       if (red_ok) {
         // a task takes LPT lanes (several tasks per warp when they are small)
         const int LPT = R == 1 ? 8 : R == 2 ? 16 : 32;
         const int tpw = 32 / LPT, sub = lane / LPT, sl = lane - sub * LPT;
-        for (int k0 = cta.k0 + warp * tpw; k0 < cta.k0 + cta.nk; k0 += NVW * tpw) {
+        for (int k0 = warp * tpw; k0 < cta.nk; k0 += NVW * tpw) {
           const int k = k0 + sub;
-          if (k >= cta.k0 + cta.nk) continue;
-          const RTask tk = hd.st_task[k];
-          const YItem y = hd.st_y[tk.yi];
+          if (k >= cta.nk) continue;
+          const RTask& tk = tasks[k];
+          const YItem& y = yitems[tk.yi];
           const int E = y.rV * R;
           const W* data = part + (int64_t)y.pbase * R;
           W* const out = red_s + tk.srow * R;
@@ -497,8 +566,8 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
       }
       bar_v(NVW);
       if (red_ok) {
-        for (int i = cta.y0 + warp; i < cta.y0 + cta.ny; i += NVW) {
-          const YItem y = hd.st_y[i];
+        for (int i = warp; i < cta.ny; i += NVW) {
+          const YItem& y = yitems[i];
           const int E = y.rV * R;
           const W invs = (W)y.invs;
           for (int e = lane; e < E; e += 32) {
@@ -508,6 +577,41 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             ys_s[(y.yrow + c) * R + r] = a * invs;
           }
         }
+      }
+      bar_v(NVW);   // the Y area is complete
+    }
+    // ---- U Y of every tile into the shared-memory buffer while the leaf
+    //      blocks still stream (warp w takes the chunk's tiles w, w + NVW, ...;
+    //      lane = row); the next U chunk is copied once every V warp is done
+    //      with the current one ----
+    if (pl.uy_smem && nuch > 0) {
+      const bool compute = alive && red_ok;
+      int uc = 0;
+      for (int t = 0; t < nt; ++uc) {
+        const int t2 = next_u_chunk(tiles, t, nt, vcap);
+        const bool landed = warp_wait(ufull, uc & 1, hd.err, 6);
+        if (landed && compute) {
+          const int64_t u0 = tiles[t].uoff;
+          for (int tt = t + warp; tt < t2; tt += NVW) {
+            const StTile& tq = tiles[tt];
+            W acc[BW];
+#pragma unroll
+            for (int j = 0; j < BW; ++j) acc[j] = (W)0;
+            tile_uy<W, BW>(vu + (tq.uoff - u0), tq.hbytes, llev + tq.lleaf * depth, depth, ys_s, R, lane, xvec, acc);
+#pragma unroll
+            for (int j = 0; j < BW; ++j)
+              if (j < R) uy_s[(tt * R + j) * kTileRows + lane] = acc[j];
+          }
+        }
+        t = t2;
+        // every V warp is done with the chunk; a wait that gave up in any of
+        // them ends the stage (no copy is issued over one still in flight)
+        if (!bar_and(kBarVote, landed, 32 * NVW)) {
+          if (tid == 0) mbar_wait(ufull, uc & 1, hd.err, 6);
+          alive = false;
+          break;
+        }
+        if (tid == 0 && t < nt) copy_u_chunk(hd, tiles, t, next_u_chunk(tiles, t, nt, vcap), vu, ufull);
       }
     }
   } else {
@@ -523,7 +627,6 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     if (grp < S) {
       const int r = lane;
       W* const pbuf = reinterpret_cast<W*>(smem + pl.part_off) + (size_t)grp * 2 * 3 * kTileRows * R;   // WPS <= 4
-      const bool xvec = sizeof(W) == 4 && BW % 4 == 0 && R % 4 == 0;
       for (int tl = grp; tl < nt && alive; tl += S) {
         const bool landed = warp_wait(&full[grp], (tl / S) & 1, hd.err, 4);
         const StTile& tq = tiles[tl];
@@ -598,7 +701,7 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
               if (j < R) pb[((role - 1) * kTileRows + r) * R + j] = acc[j];
           }
           // the group's rows are in the buffer (or a wait gave up in a warp)
-          if (!(alive = group_all(grp, landed, 32 * WPS))) break;
+          if (!(alive = bar_and(kBarGroup0 + grp, landed, 32 * WPS))) break;
           if (role > 0) continue;
           for (int h = 0; h < WPS - 1; ++h)
 #pragma unroll
@@ -624,89 +727,58 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     }
   }
 
-  // ---- U phase: every D X is in place and every Y is in shared memory.
-  //      For each U chunk (the header and U rows of consecutive tiles, in
-  //      the V/U area), warp w takes the chunk's tiles w, w + 16, ...,
-  //      lane = row: B[row] = D X + sum over levels of U[row, :] Y (U column
-  //      by column, 32 rows per column; Y rows are broadcasts) ----
-  bar_cons();
-  {
-    const int r = lane;
-    const bool xvec = sizeof(W) == 4 && BW % 4 == 0 && R % 4 == 0;
-    int uc = 0;
-    for (int t = 0; t < nt; ++uc) {
-      const int t2 = nuch > 0 ? next_u_chunk(tiles, t, nt, vcap) : nt;
-      bool landed = true;
-      if (nuch > 0) landed = warp_wait(ufull, uc & 1, hd.err, 6);
-      if (landed && alive) {
-        const int64_t u0 = nuch > 0 ? tiles[t].uoff : 0;
-        for (int tt = t + warp; tt < t2; tt += kSWarps) {
-          const StTile& tq = tiles[tt];
-          const uint8_t* const st = vu + (tq.uoff - u0);
-          const int hbytes = tq.hbytes;
-          W acc[BW];
-          if (pl.res_smem) {
+  bar_cons();   // every D X and every U Y (or every Y) is in place
+  const int r = lane;
+  if (pl.uy_smem) {
+    // ---- final pass: B[rows] = D X + U Y, warp w takes tiles w, w + 16, ... ----
+    const bool have_uy = nuch > 0;
+    for (int tt = warp; tt < nt; tt += kSWarps) {
+      const StTile& tq = tiles[tt];
+      W* brow = B + (int64_t)(tq.row0 + min(r, tq.rows - 1)) * ldb;
+      W acc[BW];
 #pragma unroll
-            for (int j = 0; j < BW; ++j) acc[j] = j < R ? res_s[(tt * R + j) * kTileRows + r] : (W)0;
-          } else {
-            W* brow = B + (int64_t)(tq.row0 + min(r, tq.rows - 1)) * ldb;
+      for (int j = 0; j < BW; ++j)
+        acc[j] = j < R ? (pl.res_smem ? res_s[(tt * R + j) * kTileRows + r] : brow[j]) : (W)0;
+      if (have_uy) {
 #pragma unroll
-            for (int j = 0; j < BW; ++j) acc[j] = j < R ? brow[j] : (W)0;
-          }
-          for (int k = 1; k <= depth && nuch > 0; ++k) {
-            const uint2 hw = reinterpret_cast<const uint2*>(st)[k - 1];
-            const uint32_t w0 = hw.x, w1 = hw.y;
-            const int ru = (int)(w1 & 0xffffu), tier = (int)(w1 >> 16);
-            if (ru == 0) continue;
-            const int yrow = llev[tq.lleaf * depth + (k - 1)].yrow;
-            const W* const yb = ys_s + yrow * R;
-            // Y rows are read BW values wide (values past R are never stored)
-            auto level = [&](auto tc) {
-              constexpr int TIER = decltype(tc)::value;
-              constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
-              const uint8_t* const ucol = st + hbytes + w0 + r * eb;
-              if (xvec) {
-#pragma unroll 4
-                for (int c = 0; c < ru; ++c) {
-                  const W u = ldf<W, TIER>(ucol + c * kTileRows * eb);
-                  W yv[BW];
-                  ld_row<W, BW, true>(yb + c * R, yv);
-#pragma unroll
-                  for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
-                }
-              } else {
-#pragma unroll 4
-                for (int c = 0; c < ru; ++c) {
-                  const W u = ldf<W, TIER>(ucol + c * kTileRows * eb);
-                  W yv[BW];
-                  ld_row<W, BW, false>(yb + c * R, yv);
-#pragma unroll
-                  for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
-                }
-              }
-            };
-            with_format(tier, level);
-          }
-          if (r < tq.rows) {
-            W* brow = B + (int64_t)(tq.row0 + r) * ldb;
-            if (xvec && ldb % 4 == 0 && (reinterpret_cast<uintptr_t>(brow) & 15) == 0) {
-#pragma unroll
-              for (int j4 = 0; j4 < BW / 4; ++j4)
-                *reinterpret_cast<float4*>(brow + 4 * j4) =
-                    make_float4(acc[4 * j4], acc[4 * j4 + 1], acc[4 * j4 + 2], acc[4 * j4 + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < BW; ++j)
-                if (j < R) brow[j] = acc[j];
-            }
-          }
-        }
+        for (int j = 0; j < BW; ++j)
+          if (j < R) acc[j] += uy_s[(tt * R + j) * kTileRows + r];
       }
-      t = t2;
-      if (nuch > 0) {
-        bar_cons();   // every warp is done with the chunk
-        if (tid == 0 && t < nt) copy_u_chunk(hd, tiles, t, next_u_chunk(tiles, t, nt, vcap), vu, ufull);
+      if (r < tq.rows) store_brow<W, BW>(brow, R, xvec, ldb, acc);
+    }
+    return;
+  }
+  // ---- U phase without the buffer: for each U chunk (the header and U
+  //      rows of consecutive tiles, in the V/U area), warp w takes the
+  //      chunk's tiles w, w + 16, ...: B[row] = D X + U Y ----
+  int uc = 0;
+  for (int t = 0; t < nt; ++uc) {
+    const int t2 = nuch > 0 ? next_u_chunk(tiles, t, nt, vcap) : nt;
+    bool landed = true;
+    if (nuch > 0) landed = warp_wait(ufull, uc & 1, hd.err, 6);
+    if (landed && alive) {
+      const int64_t u0 = nuch > 0 ? tiles[t].uoff : 0;
+      for (int tt = t + warp; tt < t2; tt += kSWarps) {
+        const StTile& tq = tiles[tt];
+        W* brow = B + (int64_t)(tq.row0 + min(r, tq.rows - 1)) * ldb;
+        W acc[BW];
+#pragma unroll
+        for (int j = 0; j < BW; ++j)
+          acc[j] = j < R ? (pl.res_smem ? res_s[(tt * R + j) * kTileRows + r] : brow[j]) : (W)0;
+        if (nuch > 0)
+          tile_uy<W, BW>(vu + (tq.uoff - u0), tq.hbytes, llev + tq.lleaf * depth, depth, ys_s, R, r, xvec, acc);
+        if (r < tq.rows) store_brow<W, BW>(brow, R, xvec, ldb, acc);
       }
+    }
+    t = t2;
+    if (nuch > 0) {
+      // every warp is done with the chunk; a wait that gave up in any warp
+      // ends the phase (no copy is issued over one still in flight)
+      if (!bar_and(kBarCons, landed, kSThreads)) {
+        if (tid == 0) mbar_wait(ufull, uc & 1, hd.err, 6);
+        break;
+      }
+      if (tid == 0 && t < nt) copy_u_chunk(hd, tiles, t, next_u_chunk(tiles, t, nt, vcap), vu, ufull);
     }
   }
 }
@@ -735,9 +807,10 @@ int smem_limit() {
 }
 
 // Shared memory of a launch with R columns of es bytes: the leaf-block ring,
-// the V/U area, the D X results of the CTA's tiles (when they fit), the D
-// groups' partial rows, the V running sums carried across V chunks, the Y
-// area, the reduction scratch, the barriers and the tile metadata.
+// the V/U area, the D X results and the U Y of the CTA's tiles (when they
+// fit), the D groups' partial rows, the V running sums carried across V
+// chunks, the Y area, the reduction scratch, the barriers and the CTA's
+// record.
 SPlan make_plan(const HandleDev& hd, int R, int es, bool xstaged) {
   SPlan p;
   memset(&p, 0, sizeof(p));
@@ -753,29 +826,31 @@ SPlan make_plan(const HandleDev& hd, int R, int es, bool xstaged) {
   const int acc_b = al16(std::max(hd.st_acc_rows, 1) * R * es);
   const int ys_b = al16(std::max(hd.st_y_rows, 1) * R * es);
   const int red_b = al16(std::max(hd.st_red_rows, 1) * R * es);
-  const int bar_b = (2 * kSStagesMax + 2) * 8 + 16;   // the barriers and the grid-counter flag
-  const int meta_b = al16(hd.st_max_tiles * (int)sizeof(StTile)) +
-                     al16(hd.st_max_leaves * std::max(hd.depth, 1) * (int)sizeof(StLev)) + al16((hd.depth + 1) * 4);
+  const int bar_b = (2 * kSStagesMax + 3) * 8 + 16;   // the barriers and the grid-counter flag
+  const int meta_b = al16(hd.st_blob_stride);
   const int part_stage = 2 * 3 * kTileRows * R * es;   // up to three helpers, two buffers (four warps)
-  // V warps: the V phase and the reduction are the critical path for one or
-  // two columns; with more columns the leaf-block products take more warps
-  p.nvw = R <= 2 ? 8 : 4;
+  // eight V warps (V phase, reduction, U Y: the critical path), eight D warps
+  p.nvw = 8;
   const int ndw = kSWarps - p.nvw;
   const int fixed0 = acc_b + ys_b + red_b + bar_b + meta_b;
   const int room = smem_limit() - fixed0;
   // the V/U area takes what three stages leave, down to one tile's worth;
-  // the D X results stay in shared memory if two stages still fit beside them
+  // the D X results, then the U Y, stay in shared memory if two stages
+  // still fit beside them
   vu = std::max(vu_min, std::min(vu, room - 3 * (sb + part_stage)));
   vu = al16(vu);
   p.res_smem = room - vu - res_b >= 2 * (sb + part_stage) ? 1 : 0;
-  const int room2 = room - vu - (p.res_smem ? res_b : 0);
+  p.uy_smem = p.res_smem && room - vu - 2 * res_b >= 2 * (sb + part_stage) ? 1 : 0;
+  const int room2 = room - vu - (p.res_smem ? res_b : 0) - (p.uy_smem ? res_b : 0);
   p.nstages = std::min(kSStagesMax, room2 / (sb + part_stage));
   p.wps = std::max(1, std::min(4, ndw / std::max(p.nstages, 1)));
+  p.dmax = kSInflight;
   p.vu_bytes = vu;
   const int ring = std::max(p.nstages, 0) * sb;
   p.vu_off = ring;
   p.res_off = al16(p.vu_off + vu);
-  p.part_off = al16(p.res_off + (p.res_smem ? res_b : 0));
+  p.uy_off = al16(p.res_off + (p.res_smem ? res_b : 0));
+  p.part_off = al16(p.uy_off + (p.uy_smem ? res_b : 0));
   p.acc_off = al16(p.part_off + std::max(p.nstages, 0) * part_stage);
   p.ys_off = p.acc_off + acc_b;
   p.red_off = p.ys_off + ys_b;
