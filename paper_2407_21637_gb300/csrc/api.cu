@@ -315,7 +315,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   std::vector<std::pair<int64_t, uint32_t>> headers;   // (byte offset in pool, word)
   int max_nq = 0, max_region = 0;
   std::vector<int> leaf_nq(nleaves, 0), leaf_yrow(nleaves, 0), leaf_tile0(nleaves + 1, 0);
-  std::vector<std::vector<int>> leaf_anc(nleaves), leaf_vseg(nleaves);
+  std::vector<std::vector<int>> leaf_anc(nleaves), leaf_vseg(nleaves), leaf_useg(nleaves);
   int yrows = 0;
   const int hbytes = (int)align_up((size_t)8 * depth, 16);   // one header entry per level
   pool = align_up(pool, 256);
@@ -336,7 +336,8 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     const int mp = (int)align_up(lf.m, 4);                // D row length (zero padded)
     const int dbytes = mp * kTileRows * ebw;
     // byte offset of each level's U (V) block after the header (inside the V part)
-    std::vector<int> useg(depth + 2, 0);
+    std::vector<int>& useg = leaf_useg[l];
+    useg.assign(depth + 2, 0);
     std::vector<int>& vseg = leaf_vseg[l];
     vseg.assign(depth + 2, 0);
     for (int k = 1; k <= depth; ++k) {
@@ -750,6 +751,10 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   std::vector<YItem> st_y;
   std::vector<hodlr::RTask> st_task;
   std::vector<hodlr::StCta> st_cta(st_grid);
+  // per CTA: its leaves' records and U columns
+  std::vector<std::vector<hodlr::StLeaf>> st_leaf(st_grid);
+  std::vector<std::vector<std::vector<hodlr::StCol>>> st_ucol(st_grid);
+  int st_max_nu = 0;
   int st_y_rows = 0, st_red_rows = 0, st_max_tiles = 0, st_max_leaves = 0, st_max_vbytes = 0, st_max_cta_v = 0;
   int st_max_cta_xrows = 0, st_max_tile_bytes = 0, st_max_cta_u = 0, st_max_ubytes = 0, st_max_d2bytes = 0;
   for (int c = 0; c < st_grid; ++c) {
@@ -799,10 +804,20 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       rec.rows = (int16_t)tl.rows;
       if (l == last_leaf) {
         rec.lleaf = (int16_t)(nl - 1);
+        ++st_leaf[c].back().nt;
         continue;   // the leaf's level entries are in place
       }
       last_leaf = l;
       rec.lleaf = (int16_t)nl++;
+      {
+        hodlr::StLeaf lr;
+        memset(&lr, 0, sizeof(lr));
+        lr.t0 = (int16_t)(t - sc.t0);
+        lr.nt = 1;
+        lr.utier = -2;   // no column yet
+        st_leaf[c].push_back(lr);
+        st_ucol[c].emplace_back();
+      }
       stlev.resize(stlev.size() + depth);
       for (int k = 1; k <= depth; ++k) {
         const int a = leaf_anc[l][k];
@@ -835,6 +850,23 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
         }
         e.yrow = it->second;
       }
+      // the leaf's U columns, level by level
+      hodlr::StLeaf& lr = st_leaf[c].back();
+      for (int k = 1; k <= depth; ++k) {
+        const NodeDev& na = h->nodes[leaf_anc[l][k]];
+        const StLev& e = stlev[stlev.size() - depth + (k - 1)];
+        for (int cc = 0; cc < na.rU; ++cc) {
+          hodlr::StCol col;
+          col.off = tl.hbytes + leaf_useg[l][k] + cc * kTileRows * prec_bytes(na.tierU);
+          col.idx = (uint16_t)(e.yrow + cc);
+          col.k = (uint8_t)k;
+          col.tier = (uint8_t)na.tierU;
+          st_ucol[c].back().push_back(col);
+          lr.utier = lr.utier == -2 || lr.utier == na.tierU ? (int16_t)na.tierU : (int16_t)-1;
+        }
+      }
+      lr.nu = (int32_t)st_ucol[c].back().size();
+      st_max_nu = std::max(st_max_nu, lr.nu);
     }
     sc.nl = nl;
     st_max_leaves = std::max(st_max_leaves, nl);
@@ -897,7 +929,10 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   const int off_acc = off_lev + (int)align_up((size_t)st_max_leaves * dl * sizeof(StLev), 16);
   const int off_task = off_acc + (int)align_up((size_t)(depth + 1) * sizeof(int32_t), 16);
   const int off_y = off_task + (int)align_up((size_t)st_max_nk * sizeof(hodlr::RTask), 16);
-  const int blob_stride = (int)align_up((size_t)off_y + (size_t)st_max_ny * sizeof(YItem), 16);
+  const int off_leaf = off_y + (int)align_up((size_t)st_max_ny * sizeof(YItem), 16);
+  const int leaf_stride =
+      (int)align_up(sizeof(hodlr::StLeaf) + (size_t)st_max_nu * sizeof(hodlr::StCol), 16);
+  const int blob_stride = off_leaf + st_max_leaves * leaf_stride;
   std::vector<uint8_t> blob((size_t)blob_stride * st_grid, 0);
   for (int c = 0; c < st_grid; ++c) {
     const hodlr::StCta& sc = st_cta[c];
@@ -908,6 +943,12 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
     memcpy(b + off_acc, st_accoff.data(), sizeof(int32_t) * (depth + 1));
     if (sc.nk) memcpy(b + off_task, &st_task[sc.k0], sizeof(hodlr::RTask) * sc.nk);
     if (sc.ny) memcpy(b + off_y, &st_y[sc.y0], sizeof(YItem) * sc.ny);
+    for (size_t u = 0; u < st_leaf[c].size(); ++u) {
+      uint8_t* lb = b + off_leaf + u * leaf_stride;
+      memcpy(lb, &st_leaf[c][u], sizeof(hodlr::StLeaf));
+      hodlr::StCol* cols = reinterpret_cast<hodlr::StCol*>(lb + sizeof(hodlr::StLeaf));
+      if (!st_ucol[c][u].empty()) memcpy(cols, st_ucol[c][u].data(), sizeof(hodlr::StCol) * st_ucol[c][u].size());
+    }
   }
   if ((st = upload(blob, &h->d_st_blob)) != HODLR_OK) return st;
   // gathered Y: yrows rows of up to max_nrhs values, plus 16 bytes of slack
@@ -976,6 +1017,9 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
   hd.st_off_acc = off_acc;
   hd.st_off_task = off_task;
   hd.st_off_y = off_y;
+  hd.st_off_leaf = off_leaf;
+  hd.st_leaf_stride = leaf_stride;
+  hd.st_max_nu = st_max_nu;
   hd.st_max_leaves = st_max_leaves;
   hd.st_grid = st_grid;
   hd.st_p_rows = st_p_rows;

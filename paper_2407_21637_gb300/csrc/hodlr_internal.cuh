@@ -165,6 +165,24 @@ struct StLev {
   uint16_t rV;                    // rank of V of the ancestor
   uint8_t tierV, pad_;            // its storage format
 };
+// Per (CTA, one of its leaves): the leaf's tiles in the CTA and its U
+// columns (over the levels 1..depth, level by level) with the storage
+// format they all share (-1 if they do not), followed in the CTA's record by
+// the columns themselves (StCol).
+struct StLeaf {
+  int32_t nu;                     // U columns
+  int16_t t0, nt;                 // its tiles: CTA-local tiles t0 .. t0 + nt - 1
+  int16_t utier, pad0_;           // common format of its U columns, or -1
+  int32_t pad1_;
+};
+// One U column of a tile's U region: byte offset of its row 0 inside the
+// region (header included), the row of Y it multiplies in the CTA's Y area,
+// its level and format.
+struct StCol {
+  int32_t off;
+  uint16_t idx;
+  uint8_t k, tier;
+};
 // One Y_j a CTA needs for its U Y products: Y_j = invs * (sum of the
 // partial slots of node j), the slots of the CTAs that hold rows of j, in CTA
 // order.  The sum is split into tasks of at most kRedSlots slots whose
@@ -190,7 +208,8 @@ struct RTask {
 // (StTile[nt] at st_off_tile), its leaves' level entries (StLev[nl * depth]
 // at st_off_lev), the accumulator offsets (int32[depth + 1] at st_off_acc),
 // its reduction tasks (RTask[nk] at st_off_task) and its Y items (YItem[ny]
-// at st_off_y).
+// at st_off_y), then one column record per leaf (at st_off_leaf, stride
+// st_leaf_stride).
 struct StCta {
   int64_t voff;                   // first byte of its tiles' V parts (contiguous)
   int64_t uoff;                   // first byte of its tiles' header + U regions (contiguous)
@@ -241,6 +260,8 @@ struct HandleDev {
   const uint8_t* st_blob;         // [st_grid] records of st_blob_stride bytes (see StCta)
   int32_t st_blob_stride;         // bytes per record (a multiple of 16)
   int32_t st_off_tile, st_off_lev, st_off_acc, st_off_task, st_off_y;   // sections of a record
+  int32_t st_off_leaf, st_leaf_stride;   // per-leaf column records (StLeaf, StCol[st_max_nu])
+  int32_t st_max_nu;              // most U columns of one leaf
   int32_t st_grid;                // CTAs of the launch (one per SM)
   int32_t st_p_rows;              // rows of the partial buffer
   int32_t st_y_rows;              // rows of the largest per-CTA Y area

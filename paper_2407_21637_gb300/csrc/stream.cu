@@ -250,6 +250,61 @@ __device__ __forceinline__ void tile_uy(const uint8_t* st, int hbytes, const StL
   }
 }
 
+// Unroll factor of a loop whose step holds one BW-wide row of X or Y: as
+// many loads in flight as the registers allow.
+template <int BW>
+__host__ __device__ constexpr int unroll_for() {
+  return BW >= 16 ? 1 : BW >= 8 ? 2 : BW >= 4 ? 4 : 8;
+}
+
+// The same sum over the U columns of a leaf whose columns share one format:
+// the columns in level order (the order of tile_uy), each a byte offset in
+// the tile's U region and the row of Y it multiplies.
+template <typename W, int BW, int TIER>
+__device__ __forceinline__ void uy_flat(const uint8_t* st, const StCol* uc, int nu, const W* ys_s, int R, int r,
+                                        bool xvec, W (&acc)[BW]) {
+  constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+  const uint8_t* const rowp = st + r * eb;
+  constexpr int kUnroll = unroll_for<BW>();
+  if (xvec) {
+#pragma unroll kUnroll
+    for (int i = 0; i < nu; ++i) {
+      const StCol e = uc[i];
+      const W u = ldf<W, TIER>(rowp + e.off);
+      W yv[BW];
+      ld_row<W, BW, true>(ys_s + e.idx * R, yv);
+#pragma unroll
+      for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
+    }
+  } else {
+#pragma unroll kUnroll
+    for (int i = 0; i < nu; ++i) {
+      const StCol e = uc[i];
+      const W u = ldf<W, TIER>(rowp + e.off);
+      W yv[BW];
+      ld_row<W, BW, false>(ys_s + e.idx * R, yv);
+#pragma unroll
+      for (int j = 0; j < BW; ++j) acc[j] = fma(u, yv[j], acc[j]);
+    }
+  }
+}
+// U Y of one tile of the leaf whose record is at lrec (StLeaf, then its U
+// columns): the flat loop when its U columns share one format, else level by
+// level.
+template <typename W, int BW>
+__device__ __forceinline__ void tile_uy_any(const uint8_t* st, const StTile& tq, const uint8_t* lrec,
+                                            const StLev* llev, int depth, const W* ys_s, int R, int r, bool xvec,
+                                            W (&acc)[BW]) {
+  const StLeaf& lh = *reinterpret_cast<const StLeaf*>(lrec);
+  if (lh.nu == 0) return;
+  if (lh.utier >= 0) {
+    const StCol* const uc = reinterpret_cast<const StCol*>(lrec + sizeof(StLeaf));
+    with_format(lh.utier, [&](auto tc) { uy_flat<W, BW, decltype(tc)::value>(st, uc, lh.nu, ys_s, R, r, xvec, acc); });
+  } else {
+    tile_uy<W, BW>(st, tq.hbytes, llev + tq.lleaf * depth, depth, ys_s, R, r, xvec, acc);
+  }
+}
+
 // B row r of a tile (tile rows only), as 16-byte vectors where aligned
 template <typename W, int BW>
 __device__ __forceinline__ void store_brow(W* brow, int R, bool xvec, int64_t ldb, const W (&acc)[BW]) {
@@ -315,6 +370,7 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   const int32_t* const accoff = reinterpret_cast<const int32_t*>(meta + hd.st_off_acc);
   const RTask* const tasks = reinterpret_cast<const RTask*>(meta + hd.st_off_task);
   const YItem* const yitems = reinterpret_cast<const YItem*>(meta + hd.st_off_y);
+  const uint8_t* const leafs = meta + hd.st_off_leaf;   // per-leaf column records
   const int nt = cta.nt;
   const int xrow_bytes = pl.xstaged ? R * es : 0;
   // the whole V range of this CTA in one chunk when it fits
@@ -376,16 +432,16 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
   if (warp < NVW) {
     // ================= V warps =================
     const int kl = lane / LC, cl = lane - (lane / LC) * LC;   // lane = kl * LC + cl
-    // ---- V phase.  Item (k, p) = V columns 8p .. 8p + 7 of the level-k
-    //      ancestors, for all tiles in order; lane (kl, cl) sums rows kl,
-    //      kl + LK, ... of every tile (V column by column: consecutive rows
-    //      across the lanes) for CPL right-hand sides, so a warp reads eight
-    //      V columns and X once per row.  The sums of a node run on in
-    //      registers across its tiles; at the node's last tile in a chunk
-    //      the lanes are added (fixed butterfly) and the sum goes to the
-    //      node's slot (carried in shared memory across V chunks) ----
     if (nvch > 0) {
-      constexpr int kVC = 8;   // V columns per item
+      // ---- V phase.  Item (k, p) = V columns kVC p .. kVC p + kVC - 1 of the
+      //      level-k ancestors, for all tiles in order; lane (kl, cl) sums
+      //      rows kl, kl + LK, ... of every tile (V column by column:
+      //      consecutive rows across the lanes) for CPL right-hand sides, so a
+      //      warp reads kVC V columns and X once per row.  The sums of a node run on in
+      //      registers across its tiles; at the node's last tile in a chunk
+      //      the lanes are added (fixed butterfly) and the sum goes to the
+      //      node's slot (carried in shared memory across V chunks) ----
+      constexpr int kVC = CPL >= 4 ? 4 : 8;   // V columns per item (registers: kVC * CPL sums)
       const int passes = (hd.st_max_rank + kVC - 1) / kVC;
       const int nitems = depth * passes;
       int c_idx = 0;
@@ -597,7 +653,8 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
             W acc[BW];
 #pragma unroll
             for (int j = 0; j < BW; ++j) acc[j] = (W)0;
-            tile_uy<W, BW>(vu + (tq.uoff - u0), tq.hbytes, llev + tq.lleaf * depth, depth, ys_s, R, lane, xvec, acc);
+            tile_uy_any<W, BW>(vu + (tq.uoff - u0), tq, leafs + (size_t)tq.lleaf * hd.st_leaf_stride,
+                               llev, depth, ys_s, R, lane, xvec, acc);
 #pragma unroll
             for (int j = 0; j < BW; ++j)
               if (j < R) uy_s[(tt * R + j) * kTileRows + lane] = acc[j];
@@ -766,7 +823,8 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
         for (int j = 0; j < BW; ++j)
           acc[j] = j < R ? (pl.res_smem ? res_s[(tt * R + j) * kTileRows + r] : brow[j]) : (W)0;
         if (nuch > 0)
-          tile_uy<W, BW>(vu + (tq.uoff - u0), tq.hbytes, llev + tq.lleaf * depth, depth, ys_s, R, r, xvec, acc);
+          tile_uy_any<W, BW>(vu + (tq.uoff - u0), tq, leafs + (size_t)tq.lleaf * hd.st_leaf_stride,
+                             llev, depth, ys_s, R, r, xvec, acc);
         if (r < tq.rows) store_brow<W, BW>(brow, R, xvec, ldb, acc);
       }
     }
@@ -774,7 +832,7 @@ stream_kernel(const HandleDev hd, const W* __restrict__ X, int64_t ldx, int R, W
     if (nuch > 0) {
       // every warp is done with the chunk; a wait that gave up in any warp
       // ends the phase (no copy is issued over one still in flight)
-      if (!bar_and(kBarCons, landed, kSThreads)) {
+      if (!bar_and(kBarConsVote, landed, kSThreads)) {
         if (tid == 0) mbar_wait(ufull, uc & 1, hd.err, 6);
         break;
       }
