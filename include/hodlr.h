@@ -292,6 +292,12 @@ hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out);
  * format (hodlr_prec) and rank of block (i, i^1).  Either output may be NULL. */
 hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks);
 
+/* hodlr_node_sizes -- per node (layout as ranks in hodlr_import: node
+ * q = 2^k - 2 + i is (k, i), k = 1..depth) its first row and its rows, the
+ * ceil-half cluster tree of Def. 2.1 (the leaves are the level-depth nodes;
+ * with depth 0 the one leaf is rows [0, n)).  Either output may be NULL. */
+hodlr_status hodlr_node_sizes(hodlr_t h, int32_t* row0, int32_t* m);
+
 /* hodlr_dense_kernel_matvec -- on-the-fly FP64 dense product b = A x for a
  * kernel matrix A_ij = f(x_i, x_j) + diag * delta_ij, used to check HODLR
  * products at sizes where A cannot be stored (its entries are generated in
@@ -311,6 +317,69 @@ hodlr_status hodlr_dense_kernel_matvec(int32_t n, int32_t dim, const double* poi
                                        int32_t nrows, const int32_t* rows,
                                        int32_t nrhs, const double* X, int64_t ldx,
                                        double* B, int64_t ldb, void* stream);
+
+/* ---- HODLR LU and solves (Sect. 3.4) ------------------------------------- */
+
+/* hodlr_lu -- HODLR_LU (Algorithm 3.4) of the stored matrix H-hat (its
+ * generators and leaves decoded to fp64), in fp64 on the device, kept in
+ * the handle (a previous factorization is replaced).  At every node with
+ * children a, b: the LU of H_aa, U12 = L_aa^{-1} H_ab and L21 = H_ba U_aa^{-1}
+ * on the generators, and the Schur complement H_bb - L21 U12 truncated back
+ * to the HODLR format (Assumption 3.6): every off-diagonal block inside b is
+ * recompressed with the per-block relative Frobenius tolerance eps_lu (the
+ * truncation rule of the construction, Def. 2.3); leaves are updated
+ * exactly.  eps_lu = 0 keeps every nonzero singular value.  Leaves are
+ * factored without pivoting (the block LU needs nonsingular leading blocks,
+ * as for the diagonally dominant kernel matrices of Sect. 4).  Waits for
+ * `stream`.  The current device must be the handle's.
+ * Errors: HODLR_EINVAL (eps_lu outside [0, 1), another device),
+ * HODLR_ESINGULAR (zero pivot in a leaf), HODLR_EACCURACY (a recompressed
+ * block needs more columns than the factor storage holds: at least
+ * max(64, 4 r + 32), r the largest stored rank), HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_lu(hodlr_t h, double eps_lu, void* stream);
+
+/* hodlr_lu_solve -- X = U^{-1} L^{-1} B with the factors of hodlr_lu
+ * (forward substitution with L, back substitution with U, both recursive
+ * over the tree).  B, X device fp64 (n, nrhs) row-major, ldb, ldx >= nrhs;
+ * X == B solves in place.  Enqueued on `stream`.
+ * Errors: HODLR_ENOTFACTORED, HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_lu_solve(hodlr_t h, int32_t nrhs, const double* B, int64_t ldb,
+                            double* X, int64_t ldx, void* stream);
+
+typedef struct {
+  int32_t iterations;     /* refinement steps taken */
+  int32_t gmres_steps;    /* GMRES steps, summed over the refinement steps
+                             (the most of any column in each) */
+  double backward_error;  /* ||B - H X||_F / (||H||_F ||X||_F) of the result */
+} hodlr_solve_stats;
+
+/* hodlr_solve -- H-hat X = B by GMRES-based iterative refinement with the
+ * factors of hodlr_lu as preconditioner (Sect. 3.4): X_0 = (LU)^{-1} B;
+ * then, while the normwise backward error ||B - H X||_F / (||H||_F ||X||_F)
+ * (residual in fp64 by hodlr_matvec) exceeds tol and fewer than max_it steps
+ * were taken: per column, GMRES (restart 60, modified Gram-Schmidt Arnoldi,
+ * left preconditioned by the LU solve) on H D = R to a relative
+ * preconditioned residual of 1e-4, and X += D.  The handle's working
+ * precision must be fp64.  B, X device fp64 (n, nrhs) row-major.  stats may
+ * be NULL.  Waits for `stream` (the Arnoldi scalars go to the host).
+ * Errors: HODLR_ENOTFACTORED, HODLR_EINVAL, HODLR_EACCURACY (tol not reached
+ * within max_it; X holds the last iterate), HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_solve(hodlr_t h, int32_t nrhs, const double* B, int64_t ldb,
+                         double* X, int64_t ldx, double tol, int32_t max_it,
+                         hodlr_solve_stats* stats, void* stream);
+
+/* hodlr_lu_export -- the factors of hodlr_lu on the host, in the layout of
+ * hodlr_import: ranks_u[q], ranks_v[q] = the columns of U_q and V_q now;
+ * U[q] (m_q x ranks_u[q]) and V[q] (m_q x ranks_v[q]) row-major, where for a
+ * left child a of children (a, b) U_a holds L_aa^{-1} U_a (so the upper block
+ * of U is U_a V_b^T) and V_a holds U_aa^{-T} V_a (the lower block of L is
+ * U_b V_a^T); D[l] (m_l x m_l) the leaf's LU (unit lower L below the
+ * diagonal, U on and above it).  Any output pointer may be NULL (ranks first,
+ * then buffers of the right size).  Waits for `stream`.
+ * Errors: HODLR_ENOTFACTORED, HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_lu_export(hodlr_t h, int32_t* ranks_u, int32_t* ranks_v,
+                             double* const* U, double* const* V, double* const* D,
+                             void* stream);
 
 /* hodlr_destroy -- free the handle and its device memory (synchronises the
  * device work the handle owns).  NULL is a no-op. */

@@ -49,6 +49,11 @@ class BuildOpts(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("gmres_steps", ctypes.c_int32),
+                ("backward_error", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); every symbol the header declares
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -73,10 +78,16 @@ SIGNATURES = {
     "hodlr_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
     "hodlr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "hodlr_block_tiers": (ctypes.c_int, [_P, _I32P, _I32P]),
+    "hodlr_node_sizes": (ctypes.c_int, [_P, _I32P, _I32P]),
     "hodlr_dense_kernel_matvec": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_int32, _P, ctypes.c_int32, _P,
                                                  ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    "hodlr_lu": (ctypes.c_int, [_P, ctypes.c_double, _P]),
+    "hodlr_lu_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64, _P]),
+    "hodlr_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
+                                   ctypes.c_double, ctypes.c_int32, ctypes.POINTER(SolveStats), _P]),
+    "hodlr_lu_export": (ctypes.c_int, [_P, _I32P, _I32P, _DP, _DP, _DP, _P]),
     "hodlr_destroy": (None, [_P]),
     "hodlr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hodlr_last_error": (ctypes.c_char_p, []),

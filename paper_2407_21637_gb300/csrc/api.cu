@@ -1402,6 +1402,15 @@ hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks) {
   return HODLR_OK;
 }
 
+hodlr_status hodlr_node_sizes(hodlr_t h, int32_t* row0, int32_t* m) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  for (size_t q = 0; q < h->nodes.size(); ++q) {
+    if (row0) row0[q] = h->nodes[q].row0;
+    if (m) m[q] = h->nodes[q].m;
+  }
+  return HODLR_OK;
+}
+
 hodlr_status hodlr_dense_kernel_matvec(int32_t n, int32_t dim, const double* points, int32_t kind,
                                        double c, double len2, double diag, int32_t nrows,
                                        const int32_t* rows, int32_t nrhs, const double* X,

@@ -21,6 +21,11 @@ using hodlr::HandleDev;
 using hodlr::StLev;
 using hodlr::YItem;
 
+namespace hodlr {
+struct LuState;                  // HODLR LU factors and solver scratch (lu.cu)
+void lu_destroy(LuState* s);
+}  // namespace hodlr
+
 struct hodlr_s {
   std::vector<std::vector<std::pair<int, int>>> lv;  // cluster tree (row0, m) per level
   int n = 0, depth = 0, work = HODLR_FP64, per_block = 0, max_nrhs = 64;
@@ -71,8 +76,10 @@ struct hodlr_s {
   HandleDev hd{};
   cudaEvent_t prof_ev[3] = {nullptr, nullptr, nullptr};
   bool prof_on = false, prof_valid = false;
+  hodlr::LuState* lu = nullptr;           // hodlr_lu: the factors
 
   ~hodlr_s() {
+    hodlr::lu_destroy(lu);
     for (cudaEvent_t& e : prof_ev)
       if (e) cudaEventDestroy(e);
     cudaFree(d_pool);

@@ -11,7 +11,7 @@ from typing import Sequence
 import numpy as np
 import torch
 
-from ._lib import PREC, PREC_NAME, BuildOpts, Info, Kernel, Opts, check, load
+from ._lib import PREC, PREC_NAME, BuildOpts, Info, Kernel, Opts, SolveStats, check, load
 
 _TORCH_DTYPE = {"fp64": torch.float64, "fp32": torch.float32}
 
@@ -34,18 +34,6 @@ def _dptr_array(mats: Sequence):
         keep.append(a)
         arr[i] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     return arr, keep
-
-
-def tree_sizes(n: int, depth: int):
-    """Node sizes of the ceil-half cluster tree (levels[k][i] = (row0, m))."""
-    levels = [[(0, n)]]
-    for _ in range(depth):
-        nxt = []
-        for (s, m) in levels[-1]:
-            left = (m + 1) // 2
-            nxt += [(s, left), (s + left, m - left)]
-        levels.append(nxt)
-    return levels
 
 
 class HodlrMatrix:
@@ -195,9 +183,21 @@ class HodlrMatrix:
         check(load().hodlr_block_tiers(self._h, t, r), "hodlr_block_tiers")
         return [PREC_NAME[t[q]] for q in range(nn)], [r[q] for q in range(nn)]
 
+    def node_sizes(self):
+        """The cluster tree from the library (hodlr_node_sizes): levels[k][i] =
+        (first row, rows) of node (k, i); levels[0] = [(0, n)]."""
+        nn = (1 << (self.depth + 1)) - 2
+        r0 = (ctypes.c_int32 * max(nn, 1))()
+        mm = (ctypes.c_int32 * max(nn, 1))()
+        check(load().hodlr_node_sizes(self._h, r0, mm), "hodlr_node_sizes")
+        levels = [[(0, self.n)]]
+        for k in range(1, self.depth + 1):
+            levels.append([(r0[(1 << k) - 2 + i], mm[(1 << k) - 2 + i]) for i in range(1 << k)])
+        return levels
+
     def export(self, stream=None):
         """Stored generators decoded to fp64 (hodlr_export): (U, V, D) lists."""
-        lv = tree_sizes(self.n, self.depth)
+        lv = self.node_sizes()
         _tiers, ranks = self.block_tiers()
         U, V = [], []
         for k in range(1, self.depth + 1):
@@ -212,6 +212,71 @@ class HodlrMatrix:
         pd, _ = _dptr_array(D)
         check(load().hodlr_export(self._h, pu, pv, pd, _stream_ptr(stream)), "hodlr_export")
         return U, V, D
+
+    # ---- HODLR LU and solves (Sect. 3.4) -----------------------------------
+    def lu(self, eps_lu: float, stream=None):
+        """hodlr_lu: HODLR LU (Algorithm 3.4) with Schur complements truncated
+        to eps_lu, kept in the handle."""
+        check(load().hodlr_lu(self._h, float(eps_lu), _stream_ptr(stream)), "hodlr_lu")
+
+    @staticmethod
+    def _cols(A: torch.Tensor, n: int) -> torch.Tensor:
+        A2 = A.view(-1, 1) if A.dim() == 1 else A
+        if A2.dtype != torch.float64 or not A2.is_cuda or A2.shape[0] != n or A2.stride(1) != 1:
+            raise ValueError("expected a CUDA fp64 (n, R) tensor with unit column stride")
+        return A2
+
+    def lu_solve(self, B: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """hodlr_lu_solve: X = U^{-1} L^{-1} B."""
+        B2 = self._cols(B, self.n)
+        X = out if out is not None else torch.empty_like(B2)
+        X2 = self._cols(X, self.n)
+        R = B2.shape[1]
+        check(load().hodlr_lu_solve(self._h, R, ctypes.c_void_p(B2.data_ptr()), max(B2.stride(0), R),
+                                    ctypes.c_void_p(X2.data_ptr()), max(X2.stride(0), R), _stream_ptr(stream)),
+              "hodlr_lu_solve")
+        return X.view(-1) if B.dim() == 1 else X
+
+    def solve(self, B: torch.Tensor, tol: float = 1e-12, max_it: int = 10, out: torch.Tensor | None = None,
+              stream=None):
+        """hodlr_solve (GMRES-based iterative refinement): returns (X, status,
+        stats) where stats = {iterations, gmres_steps, backward_error};
+        status is HODLR_OK or HODLR_EACCURACY (tol not reached), other
+        statuses raise."""
+        B2 = self._cols(B, self.n)
+        X = out if out is not None else torch.empty_like(B2)
+        X2 = self._cols(X, self.n)
+        R = B2.shape[1]
+        st = SolveStats()
+        rc = load().hodlr_solve(self._h, R, ctypes.c_void_p(B2.data_ptr()), max(B2.stride(0), R),
+                                ctypes.c_void_p(X2.data_ptr()), max(X2.stride(0), R), float(tol), int(max_it),
+                                ctypes.byref(st), _stream_ptr(stream))
+        if rc not in (0, 7):
+            check(rc, "hodlr_solve")
+        stats = {"iterations": st.iterations, "gmres_steps": st.gmres_steps, "backward_error": st.backward_error}
+        return (X.view(-1) if B.dim() == 1 else X), rc, stats
+
+    def lu_export(self, stream=None):
+        """hodlr_lu_export: (ranks_u, ranks_v, U, V, D) of the factors."""
+        nn = (1 << (self.depth + 1)) - 2
+        ru = (ctypes.c_int32 * max(nn, 1))()
+        rv = (ctypes.c_int32 * max(nn, 1))()
+        lib = load()
+        null = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))()
+        check(lib.hodlr_lu_export(self._h, ru, rv, null, null, null, _stream_ptr(stream)), "hodlr_lu_export")
+        lv = self.node_sizes()
+        U, V = [], []
+        for k in range(1, self.depth + 1):
+            for i, (_s, m) in enumerate(lv[k]):
+                q = (1 << k) - 2 + i
+                U.append(np.zeros((m, ru[q])))
+                V.append(np.zeros((m, rv[q])))
+        D = [np.zeros((m, m)) for (_s, m) in lv[self.depth]]
+        pu, _ = _dptr_array(U)
+        pv, _ = _dptr_array(V)
+        pd, _ = _dptr_array(D)
+        check(lib.hodlr_lu_export(self._h, ru, rv, pu, pv, pd, _stream_ptr(stream)), "hodlr_lu_export")
+        return [ru[q] for q in range(nn)], [rv[q] for q in range(nn)], U, V, D
 
     def close(self):
         if self._h:

@@ -1,0 +1,195 @@
+"""GPU HODLR LU (Algorithm 3.4), its solves and GMRES-IR (Sect. 3.4) through
+the C ABI, against the oracle (oracle/lu.py) on the stored matrix H-hat.
+
+* With (almost) no truncation the block LU is exact and the LU without
+  pivoting is unique: the GPU factors equal the dense Doolittle LU of H-hat.
+* With truncation, Cor. 3.11's bound on ||L^U^ - H-hat||_F holds, and the
+  GPU and oracle factors solve the system alike.
+* GMRES-IR with a coarse LU reaches a 1e-12 backward error on four
+  right-hand sides (the target of the LU-solve workload: kernel
+  1/(|x_i - x_j| + 1e-3) + n delta_ij, n = 1024, leaf 64, eps = 1e-8).
+* Errors: a zero pivot is HODLR_ESINGULAR, a solve before the factorization
+  HODLR_ENOTFACTORED.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import bounds as Bd
+from oracle import compress as C
+from oracle import kernels as K
+from oracle import lu as LU
+from oracle import matvec as M
+from oracle.abi_lists import oracle_to_abi
+
+pytestmark = pytest.mark.gpu
+
+TIERS = ("fp64",)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2407_21637_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+
+
+def _pair(n, depth, eps, seed=3, c=1e-3):
+    """The oracle's HODLR matrix of the LU workload kernel and the same
+    stored matrix on the GPU."""
+    from paper_2407_21637_gb300 import HodlrMatrix
+    spec = synth.KernelSpec(K.INV_DIST, c=c, diag=float(n))
+    pts = synth.uniform_points_1d(n, seed)
+    A = K.kernel_matrix(pts, spec)
+    h = C.adaptive_hodlr(pts, spec, n, depth, eps, work="fp64", tiers=TIERS, A=A)
+    ranks, U, V, D = oracle_to_abi(h)
+    g = HodlrMatrix.from_factors(n, depth, ranks, U, V, D, eps=eps, work="fp64", tiers=TIERS)
+    return h, g
+
+
+def _stored_norm(h):
+    """||H-hat||_F from the stored factors: leaves and off-diagonal blocks
+    partition the matrix, ||U V^T||_F^2 = trace((U^T U)(V^T V))."""
+    Us, Vs, Ds = M.stored(h) if hasattr(M, "stored") else (h.Uh, h.Vh, h.Dh)
+    s = sum(float(np.sum(d * d)) for d in Ds)
+    for k in range(1, h.depth + 1):
+        for i in range(1 << k):
+            u, v = Us[k][i], Vs[k][i ^ 1]
+            s += float(np.trace((u.T @ u) @ (v.T @ v)))
+    return np.sqrt(s)
+
+
+def _assemble_factors(g):
+    """Dense L^ (unit lower) and U^ (upper) from hodlr_lu_export: leaves
+    split at the diagonal, lower blocks U_b V_a^T and upper blocks U_a V_b^T
+    of every pair of children (a, b)."""
+    ru, rv, U, V, D = g.lu_export()
+    lv = g.node_sizes()
+    n, depth = g.n, g.depth
+    Lh, Uh = np.zeros((n, n)), np.zeros((n, n))
+    for i, (s, m) in enumerate(lv[depth]):
+        Lh[s:s + m, s:s + m] = np.tril(D[i], -1) + np.eye(m)
+        Uh[s:s + m, s:s + m] = np.triu(D[i])
+    for k in range(1, depth + 1):
+        for i in range(0, 1 << k, 2):
+            a, b = (1 << k) - 2 + i, (1 << k) - 2 + i + 1
+            (sa, ma), (sb, mb) = lv[k][i], lv[k][i + 1]
+            Uh[sa:sa + ma, sb:sb + mb] = U[a] @ V[b].T
+            Lh[sb:sb + mb, sa:sa + ma] = U[b] @ V[a].T
+    return Lh, Uh, ru
+
+
+@pytest.mark.parametrize("n,depth", [(1024, 4), (1000, 4), (300, 0)])
+def test_lu_without_truncation_is_the_dense_lu(n, depth):
+    """eps_lu = 1e-15 (below fp64 rounding of the blocks): the factors are the
+    dense Doolittle LU of H-hat (unique without pivoting), L^ U^ = H-hat to
+    rounding.  n = 1000 has ragged leaves, depth 0 is one dense leaf."""
+    h, g = _pair(n, depth, 1e-8)
+    Hh = M.assemble(h)
+    g.lu(1e-15)
+    Lh, Uh, _ = _assemble_factors(g)
+    Ld, Ud = LU.doolittle(Hh)
+    nH = np.linalg.norm(Hh)
+    assert np.linalg.norm(Lh @ Uh - Hh) <= 1e-13 * nH
+    assert np.abs(Lh - Ld).max() <= 1e-11
+    assert np.abs(Uh - Ud).max() <= 1e-11 * np.abs(Ud).max()
+    g.close()
+
+
+@pytest.mark.parametrize("eps_lu", [1e-8, 1e-4])
+def test_lu_with_truncation_meets_cor_3_11(eps_lu):
+    """Schur complements truncated to eps_lu: Cor. 3.11's bound on
+    ||L^ U^ - H-hat||_F, ranks no larger than the oracle's plus a few (the
+    same rule on the same singular values up to rounding), and the GPU and
+    oracle factors give solutions that agree within the truncation."""
+    n, depth = 1024, 4
+    h, g = _pair(n, depth, 1e-8)
+    Hh = M.assemble(h)
+    g.lu(eps_lu)
+    Lh, Uh, ru = _assemble_factors(g)
+    err = np.linalg.norm(Lh @ Uh - Hh)
+    bound = Bd.lu_backward_bound(eps_lu, depth, np.linalg.norm(Hh), np.linalg.norm(Lh), np.linalg.norm(Uh))
+    assert err <= bound
+    assert err <= 50 * eps_lu * np.linalg.norm(Hh)   # far inside the bound in practice
+    Lo, Uo = LU.hodlr_lu(Hh, h.levels, eps_lu)
+    b = synth.rhs_normal(n, 1, 11, np.float64)[:, 0]
+    x_gpu = np.linalg.solve(Uh, np.linalg.solve(Lh, b))
+    x_or = LU.lu_solve(Lo, Uo, b)
+    assert np.linalg.norm(x_gpu - x_or) <= 100 * eps_lu * np.linalg.norm(x_or)
+    g.close()
+
+
+@pytest.mark.parametrize("n,depth,R", [(1024, 4, 4), (1000, 3, 1), (8192, 5, 3)])
+def test_lu_solve_matches_the_dense_solve(n, depth, R):
+    """hodlr_lu_solve with (almost) exact factors solves H-hat X = B to
+    rounding; n = 8192 runs the split reductions of the small GEMMs (node
+    blocks of 4096 rows)."""
+    h, g = _pair(n, depth, 1e-8)
+    g.lu(1e-15)
+    B = torch.from_numpy(synth.rhs_normal(n, R, 13, np.float64)).cuda()
+    X = g.lu_solve(B).cpu().numpy()
+    # backward error through the fp64 product of the stored matrix
+    HX = g.matvec(torch.from_numpy(X).cuda()).cpu().numpy()
+    Bn = B.cpu().numpy()
+    nH = _stored_norm(h)
+    be = np.linalg.norm(Bn - HX) / (nH * np.linalg.norm(X))
+    assert be <= 1e-14
+    if n <= 1024:
+        Xd = np.linalg.solve(M.assemble(h), Bn)
+        assert np.linalg.norm(X - Xd) <= 1e-11 * np.linalg.norm(Xd)
+    g.close()
+
+
+def test_gmres_ir_with_a_coarse_lu_reaches_1e_12():
+    """The LU-solve workload's target: the LU truncated at eps_lu = 1e-2 as
+    the GMRES preconditioner, fp64 residuals, four right-hand sides:
+    backward error <= 1e-12 (checked again on the host against the dense
+    H-hat) within a few refinement steps."""
+    n, depth = 1024, 4
+    h, g = _pair(n, depth, 1e-8)
+    g.lu(1e-2)
+    B = torch.from_numpy(synth.rhs_normal(n, 4, 7, np.float64)).cuda()
+    X, rc, stats = g.solve(B, tol=1e-12, max_it=8)
+    assert rc == 0, stats
+    assert stats["backward_error"] <= 1e-12 and 1 <= stats["iterations"] <= 5
+    Hh = M.assemble(h)
+    Xn, Bn = X.cpu().numpy(), B.cpu().numpy()
+    be = np.linalg.norm(Bn - Hh @ Xn) / (np.linalg.norm(Hh) * np.linalg.norm(Xn))
+    assert be <= 2e-12
+    g.close()
+
+
+def test_solve_before_lu_is_enotfactored():
+    from paper_2407_21637_gb300 import _lib
+    _h, g = _pair(256, 2, 1e-8)
+    B = torch.zeros(256, 1, dtype=torch.float64, device="cuda")
+    import ctypes
+    rc = _lib.load().hodlr_lu_solve(g._h, 1, ctypes.c_void_p(B.data_ptr()), 1, ctypes.c_void_p(B.data_ptr()), 1,
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 5   # HODLR_ENOTFACTORED
+    g.close()
+
+
+def test_zero_pivot_is_esingular():
+    """A leaf whose leading entry and first row and column are zero has no LU
+    without pivoting: HODLR_ESINGULAR, reported by the device and no fault."""
+    from paper_2407_21637_gb300 import HodlrMatrix
+    n, depth = 256, 2
+    lv = C.Hodlr(n, depth).levels
+    rng = np.random.default_rng(5)
+    ranks, U, V = [], [], []
+    for k in range(1, depth + 1):
+        for (_s, m) in lv[k]:
+            ranks.append(2)
+            U.append(np.ascontiguousarray(np.linalg.qr(rng.standard_normal((m, 2)))[0]))
+            V.append(np.ascontiguousarray(0.01 * rng.standard_normal((m, 2))))
+    D = [rng.standard_normal((m, m)) + m * np.eye(m) for (_s, m) in lv[depth]]
+    D[0][0, :] = 0.0
+    D[0][:, 0] = 0.0
+    g = HodlrMatrix.from_factors(n, depth, ranks, U, V, D, eps=1e-12, work="fp64", tiers=TIERS)
+    from paper_2407_21637_gb300._lib import HodlrError
+    with pytest.raises(HodlrError) as ei:
+        g.lu(1e-10)
+    assert ei.value.status == 6   # HODLR_ESINGULAR
+    g.close()
