@@ -71,6 +71,8 @@ HOST_AHEAD_CYCLES = 400_000   # ~0.2 ms spin before each timed product (host sub
 # only while the sources that define its kernel are the ones it was measured
 # on (SHA-256 of those files), else null.
 TRAFFIC_PER_STEP = {
+    "stream_kernel": (("hodlr_internal.cuh", "dev_common.cuh", "stream.cu"),
+                      "252a0f8a6f7f474d4e21ccb27e98493f4b0843ebad07550514969f2895a8bae1", 175477248),
 }
 
 
@@ -202,7 +204,8 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_sample(min_seconds: float = 10.0, steps: int | None = None, threads: int | None = None):
+def cpu_oracle_sample(min_seconds: float = 10.0, steps: int | None = None, threads: int | None = None,
+                      env_limited: bool = False):
     """Time the CPU oracle's Algorithm 3.3 on the bounded sample: the leading
     diagonal block of the workload (n/16 rows), built by the oracle itself.
     threads: BLAS threads of the timed products (None: the library default,
@@ -239,7 +242,10 @@ def cpu_oracle_sample(min_seconds: float = 10.0, steps: int | None = None, threa
                 break
         return times, _cpu_threads()
 
-    if threads is not None and threadpool_limits is not None:
+    if env_limited:
+        times, cores = timed()   # this process's pools were sized by the environment
+        cores = threads
+    elif threads is not None and threadpool_limits is not None:
         with threadpool_limits(limits=threads):
             times, cores = timed()
         cores = threads
@@ -253,8 +259,30 @@ def cpu_oracle_sample(min_seconds: float = 10.0, steps: int | None = None, threa
             "sample": f"oracle (numpy fp64, Algorithm 3.3) on the leading diagonal block H_11^(4) of the "
                       f"workload: n={n}, depth={depth}, same kernel/eps/formats/rule, R in {list(WL['rhs'])}; "
                       f"{len(times)} steps, {per_step * 1e3:.1f} ms/step, {cores} BLAS threads "
-                      f"(host has {os.cpu_count()} cores)",
+                      f"(host has {os.cpu_count()} cores)"
+                      + ("; child process, thread pools limited by OMP/OPENBLAS/MKL_NUM_THREADS"
+                         if env_limited else ""),
             "ms_per_step": per_step * 1e3}
+
+
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def cpu_oracle_sample_limited(min_seconds: float, threads: int):
+    """cpu_oracle_sample in a child process whose BLAS and OpenMP pools are
+    limited to `threads` by the environment (the pools size themselves when
+    numpy loads, so the limit has to be set before the process starts)."""
+    env = dict(os.environ)
+    for v in _THREAD_VARS:
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(min_seconds),
+                        "--cpu-threads", str(threads)], env=env, capture_output=True, text=True,
+                       timeout=max(120.0, 20 * min_seconds))
+    if r.returncode != 0:
+        raise RuntimeError(f"CPU sample child failed: {r.stderr[-500:]}")
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d
 
 
 def _cpu_threads() -> int:
@@ -302,6 +330,128 @@ def _build(wl, pts, work=None, tiers=None, eps=None):
     return HodlrMatrix.build(pts, wl["kind"], wl["depth"], eps if eps is not None else wl["eps"], c=wl["c"],
                              len2=wl["len2"], diag=wl["diag"], work=work or wl["work"], tiers=tiers or wl["tiers"],
                              per_block=wl["per_block"], max_nrhs=MAX_NRHS, seed=1)
+
+
+LU_WL = dict(name="inv_dist_lu_1024", n=1024, depth=4, eps=1e-8, c=1e-3, seed=1, rhs=4)
+
+
+def run_lu_block(dev, with_cpu):
+    """HODLR LU (Algorithm 3.4) and GMRES-IR on the GPU for the LU-solve
+    workload (kernel 1/(|x_i - x_j| + 1e-3) + n delta_ij on n sorted U[0,1]
+    points, leaf 64, eps 1e-8, fp64 storage and work, four N(0,1) right-hand
+    sides) and at n = 8192 (leaf 256): factorization and solve wall times
+    (host-driven recursion, device kernels), backward errors and iterations;
+    the oracle's dense-block LU and GMRES-IR timed beside at n = 1024."""
+    import torch
+
+    import synth
+    from paper_2407_21637_gb300 import HodlrMatrix
+    out = {"workload": "1/(|x_i-x_j|+1e-3) + n*I on sorted U[0,1] points, eps 1e-8, fp64, 4 RHS ~ N(0,1); "
+                       "LU truncated at eps (direct) and at 1e-2 (GMRES-IR preconditioner)", "sizes": {}}
+    for n, depth in ((LU_WL["n"], LU_WL["depth"]), (8192, 5)):
+        pts = torch.from_numpy(synth.uniform_points_1d(n, LU_WL["seed"])).to(dev)
+        g = HodlrMatrix.build(pts, 0, depth, LU_WL["eps"], c=LU_WL["c"], diag=float(n), work="fp64",
+                              tiers=("fp64",), seed=LU_WL["seed"])
+        B = torch.from_numpy(synth.rhs_normal(n, LU_WL["rhs"], LU_WL["seed"], np.float64)).to(dev)
+        row = {"depth": depth, "leaf": n >> depth}
+        for name, eps_lu in (("direct", LU_WL["eps"]), ("gmres_ir", 1e-2)):
+            g.lu(eps_lu)   # warm-up (allocations)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.lu(eps_lu)
+            torch.cuda.synchronize()
+            t_lu = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            if name == "direct":
+                X = g.lu_solve(B)
+                torch.cuda.synchronize()
+                t_s = time.perf_counter() - t0
+                HX = g.matvec(X)
+                be = float(torch.linalg.norm(B - HX) / (math.sqrt(g.info()["norm2_all"]) * torch.linalg.norm(X)))
+                row[name] = {"eps_lu": eps_lu, "lu_ms": t_lu * 1e3, "solve_ms": t_s * 1e3, "backward_error": be}
+            else:
+                X, rc, st = g.solve(B, tol=1e-12, max_it=10)
+                torch.cuda.synchronize()
+                t_s = time.perf_counter() - t0
+                row[name] = {"eps_lu": eps_lu, "lu_ms": t_lu * 1e3, "solve_ms": t_s * 1e3, "status": rc, **st}
+        out["sizes"][str(n)] = row
+        g.close()
+    if with_cpu:
+        # the oracle as it stands (dense blocks, numpy), n = 1024
+        from oracle import compress as C
+        from oracle import kernels as K
+        from oracle import lu as LU
+        from oracle import matvec as M
+        n, depth = LU_WL["n"], LU_WL["depth"]
+        spec = synth.KernelSpec(K.INV_DIST, c=LU_WL["c"], diag=float(n))
+        p = synth.uniform_points_1d(n, LU_WL["seed"])
+        A = K.kernel_matrix(p, spec)
+        h = C.adaptive_hodlr(p, spec, n, depth, LU_WL["eps"], work="fp64", tiers=("fp64",), A=A)
+        Hh = M.assemble(h)
+        Bn = synth.rhs_normal(n, LU_WL["rhs"], LU_WL["seed"], np.float64)
+        t0 = time.perf_counter()
+        Lo, Uo = LU.hodlr_lu(Hh, h.levels, 1e-2)
+        t_lu = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        _X, hist, _inner = LU.gmres_ir(Hh, Lo, Uo, Bn, tol=1e-12)
+        t_s = time.perf_counter() - t0
+        out["cpu_baseline"] = {"kind": "oracle", "n": n, "lu_ms": t_lu * 1e3, "gmres_ir_ms": t_s * 1e3,
+                               "backward_error": hist[-1], "cores": os.cpu_count()}
+    return out
+
+
+C5_WL = dict(name="inv_dist_2p20", logn=20, eps=1e-6, c=1e-4, seed=5, rhs=64)
+
+
+def run_c5_block(dev, peak, flush, stream):
+    """The n = 2^20 product (kernel 1/(|x_i - x_j| + 1e-4), leaf 256, depth 12,
+    eps 1e-6, per-block adaptive formats, fp32 work, 64 N(0,1) right-hand
+    sides): build time, device time of the product (flushed L2, CUDA events),
+    its algorithmic bytes and HBM fraction, and the relative error of 2048
+    seeded rows against the on-the-fly FP64 dense product."""
+    import torch
+
+    import synth
+    from paper_2407_21637_gb300 import HodlrMatrix, dense_kernel_matvec
+    n = 1 << C5_WL["logn"]
+    depth = C5_WL["logn"] - 8
+    R = C5_WL["rhs"]
+    pts = torch.from_numpy(synth.uniform_points_1d(n, C5_WL["seed"])).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = HodlrMatrix.build(pts, 0, depth, C5_WL["eps"], c=C5_WL["c"], diag=0.0, work="fp32", per_block=True,
+                          max_nrhs=R, seed=C5_WL["seed"])
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    info = g.info()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(C5_WL["seed"])
+    X = torch.randn(n, R, device=dev, dtype=torch.float32, generator=gen)
+    B = torch.empty_like(X)
+    ts = []
+    for it in range(8):
+        flush.zero_()
+        torch.cuda._sleep(HOST_AHEAD_CYCLES)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.matvec(X, out=B)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= 3:
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    alg = sum(kernel_bytes(info, n, R, 4, True).values())
+    rows = torch.from_numpy(np.sort(np.random.default_rng(C5_WL["seed"]).choice(n, 2048, replace=False))
+                            .astype(np.int32)).to(dev)
+    ref = dense_kernel_matvec(pts, 0, X.double(), c=C5_WL["c"], diag=0.0, rows=rows)
+    rel = float(torch.linalg.norm(B.double()[rows.long()] - ref) / torch.linalg.norm(ref))
+    g.close()
+    return {"workload": "1/(|x_i-x_j|+1e-4) on 2^20 sorted U[0,1] points, leaf 256, depth 12, eps 1e-6, "
+                        "per-block adaptive formats, fp32 work, 64 RHS ~ N(0,1)",
+            "build_s": t_build, "product_ms": ms, "alg_bytes": alg, "GBps": alg / (ms * 1e-3) / 1e9,
+            "frac_hbm": alg / (ms * 1e-3) / 1e9 / peak, "max_rank": info["max_rank"],
+            "bytes_per_tier": info["bytes_per_tier"], "rows_checked": 2048, "rel_err_rows": rel,
+            "thm_3_1_factor": (2 * math.sqrt(2 * depth) + 1) * C5_WL["eps"]}
 
 
 def run_ours(args, rank, world, dist):
@@ -538,9 +688,13 @@ def run_ours(args, rank, world, dist):
         "wall_timed_s": t_wall,
     }
     line.update(extra)
+    if rank == 0 and not args.quick:
+        line["lu_solve"] = run_lu_block(dev, with_cpu=not args.no_cpu)
+    if rank == 0 and args.c5:
+        line["c5"] = run_c5_block(dev, peak, flush, stream)
     if rank == 0 and not args.no_cpu:
         all_cores = cpu_oracle_sample(min_seconds=args.cpu_seconds)
-        one = cpu_oracle_sample(min_seconds=args.cpu_seconds / 2, threads=1)
+        one = cpu_oracle_sample_limited(args.cpu_seconds / 2, threads=1)
         all_cores.pop("ms_per_step", None)
         one.pop("ms_per_step", None)
         line["cpu_baseline"] = all_cores
@@ -560,7 +714,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and error checks")
+    ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-threads", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--c5", action="store_true",
+                    help="add the n = 2^20 product block (hodlr_build takes about ten minutes)")
     args = ap.parse_args()
+    if args.cpu_sample is not None:   # the child of cpu_oracle_sample_limited
+        print(json.dumps(cpu_oracle_sample(args.cpu_sample, threads=args.cpu_threads, env_limited=True)))
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
