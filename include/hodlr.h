@@ -292,6 +292,48 @@ hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out);
  * format (hodlr_prec) and rank of block (i, i^1).  Either output may be NULL. */
 hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks);
 
+/* ---- batched products ------------------------------------------------------ */
+
+/* A planned batch: many stored matrices (any sizes, ranks and formats; one
+ * working precision), each with its own X and B, computed by one persistent
+ * launch.  Each matrix's product (Algorithm 3.3) runs inside one CTA (V^T X
+ * per node in fixed-order partial sums, then D X + U Y per 32-row tile), so
+ * the launch has no grid-wide dependency; the matrices are dealt to the CTAs
+ * longest first by their bytes.  Results equal hodlr_matvec's within the
+ * rounding bound of the product (the sums are ordered differently). */
+typedef struct hodlr_batch_s* hodlr_batch_t;
+
+/* hodlr_batch_create -- plan a batch of `count` products B_i = H_i X_i:
+ * hs[i] (handles on the current device, all with working precision
+ * xb_prec), nrhs[i] in [1, 16], X[i] / B[i] device arrays (n_i, nrhs[i])
+ * row-major with ldx[i], ldb[i] >= nrhs[i].  Uploads the work list and
+ * allocates the scratch (Y and the partial sums of every item); the handles
+ * and X/B buffers must outlive the batch (their contents may change between
+ * runs).  One handle may appear in several items.  Synchronous.
+ * Errors: HODLR_EINVAL, HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, const int32_t* nrhs,
+                                const void* const* X, const int64_t* ldx,
+                                void* const* B, const int64_t* ldb, int32_t xb_prec,
+                                hodlr_batch_t* out);
+
+/* hodlr_batch_run -- one launch of the planned products on `stream`; threads
+ * per CTA 128, 256 or 512, or 0 for the batch's current choice (256 until
+ * hodlr_batch_tune).  Allocates nothing and copies nothing from the host, so
+ * it can be captured in a CUDA graph.  Two runs of one batch that overlap on
+ * the GPU race on its scratch.  Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_batch_run(hodlr_batch_t b, int32_t threads, void* stream);
+
+/* hodlr_batch_tune -- measured search over the CTA size (128, 256, 512
+ * threads; two warm-up and five timed runs each, CUDA events on `stream`):
+ * keeps the fastest as the batch's choice and returns it with its mean time
+ * in ms (either output may be NULL).  Runs the batch 21 times (B is
+ * overwritten).  Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_batch_tune(hodlr_batch_t b, void* stream, int32_t* best_threads, float* best_ms);
+
+/* hodlr_batch_destroy -- free the plan (synchronises its device work).  NULL
+ * is a no-op. */
+void hodlr_batch_destroy(hodlr_batch_t b);
+
 /* hodlr_node_sizes -- per node (layout as ranks in hodlr_import: node
  * q = 2^k - 2 + i is (k, i), k = 1..depth) its first row and its rows, the
  * ceil-half cluster tree of Def. 2.1 (the leaves are the level-depth nodes;

@@ -88,6 +88,12 @@ SIGNATURES = {
     "hodlr_solve": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, ctypes.c_int64,
                                    ctypes.c_double, ctypes.c_int32, ctypes.POINTER(SolveStats), _P]),
     "hodlr_lu_export": (ctypes.c_int, [_P, _I32P, _I32P, _DP, _DP, _DP, _P]),
+    "hodlr_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_P), _I32P, ctypes.POINTER(_P),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_P),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, ctypes.POINTER(_P)]),
+    "hodlr_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "hodlr_batch_tune": (ctypes.c_int, [_P, _P, _I32P, ctypes.POINTER(ctypes.c_float)]),
+    "hodlr_batch_destroy": (None, [_P]),
     "hodlr_destroy": (None, [_P]),
     "hodlr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hodlr_last_error": (ctypes.c_char_p, []),

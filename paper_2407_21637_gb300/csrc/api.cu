@@ -363,6 +363,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       tl.xrow0 = lf.row0;
       tl.nq = nq;
       tl.yrow = leaf_yrow[l];
+      tl.leaf = l;
       h->p2.push_back(tl);
       // header, two words per level k = 1..depth: byte offset of the level's
       // U block after the header; rank | format << 16

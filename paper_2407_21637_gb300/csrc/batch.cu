@@ -1,0 +1,428 @@
+// Batched HODLR products: many stored matrices (any sizes, ranks, formats;
+// one working precision), each with its own X and B, in one persistent
+// launch.  Each matrix's product (Algorithm 3.3) runs inside one CTA, so the
+// launch needs no grid-wide dependency; the matrices are dealt to the CTAs
+// longest first (by bytes) when the batch is planned.
+//
+// Per matrix, inside its CTA (warps over independent units, CTA barriers
+// between the steps, every sum in a fixed order):
+//   1. V^T X in units (node q, up to kLeavesPerUnit leaves of q's rows):
+//      lanes over rows, a warp-reduced partial per unit and column of V_q;
+//   2. Y_q = (sum of q's unit partials, in unit order) x the power-of-two
+//      scales of V_q and U_{q^1};
+//   3. per 32-row tile (lane = row): D X from the tile's interleaved
+//      leaf-block part, plus sum_k U_{a_k}[rows, :] Y_{a_k ^ 1} from the
+//      tile's header and U region (a_k the level-k ancestor of its leaf).
+//
+// hodlr_batch_create uploads the work list and allocates the scratch once;
+// hodlr_batch_run is one kernel launch that allocates and copies nothing.
+#include <algorithm>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "dev_common.cuh"
+#include "handle.cuh"
+
+namespace hodlr {
+namespace {
+
+constexpr int kLeavesPerUnit = 8;   // leaves of rows per V^T X unit
+constexpr int kBatchMaxCols = 16;   // right-hand sides per matrix at most
+
+struct BItem {
+  const uint8_t* pool;
+  const NodeDev* nodes;
+  const LeafDev* leaves;
+  const P2Tile* tiles;
+  const int4* units;      // (node, first leaf, end leaf, first partial row)
+  const int32_t* node_u;  // [nnodes + 1]: the node's units
+  const int32_t* yoff;    // [nnodes]: first row of Y_q
+  void* Y;                // rows x R
+  void* P;                // partial rows x R
+  const void* X;
+  void* B;
+  int64_t ldx, ldb;
+  int32_t depth, R, nnodes, nunits, ntiles, pad_;
+};
+
+template <typename W, int P>
+__device__ __forceinline__ W ldg_fmt(const uint8_t* p) {
+  if constexpr (P == HODLR_FP64) {
+    return (W)__ldg(reinterpret_cast<const double*>(p));
+  } else if constexpr (P == HODLR_FP32) {
+    return (W)__ldg(reinterpret_cast<const float*>(p));
+  } else if constexpr (P == HODLR_FP16) {
+    return (W)__half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
+  } else if constexpr (P == HODLR_BF16) {
+    return (W)__uint_as_float(((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p))) << 16);
+  } else {
+    const unsigned char b = __ldg(reinterpret_cast<const unsigned char*>(p));
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)b, P == HODLR_E4M3 ? __NV_E4M3 : __NV_E5M2);
+    return (W)__half2float(*reinterpret_cast<__half*>(&h));
+  }
+}
+
+template <typename W, int RB>
+__device__ __forceinline__ void ld_xrow(const W* x, int R, W (&xv)[RB]) {
+#pragma unroll
+  for (int j = 0; j < RB; ++j) xv[j] = j < R ? __ldg(x + j) : (W)0;
+}
+
+// Loads of one row step in flight: fewer as the rows get wider.
+template <int RB>
+__host__ __device__ constexpr int batch_unroll() { return RB >= 8 ? 1 : RB >= 4 ? 2 : 4; }
+
+template <typename W, int RB>
+__global__ void __launch_bounds__(512, 1)
+batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_first, const int32_t* __restrict__ cta_items) {
+  constexpr int es = sizeof(W);
+  constexpr int G16 = 16 / es;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int e = cta_first[blockIdx.x]; e < cta_first[blockIdx.x + 1]; ++e) {
+    const BItem& b = items[cta_items[e]];
+    const W* X = reinterpret_cast<const W*>(b.X);
+    W* Y = reinterpret_cast<W*>(b.Y);
+    W* P = reinterpret_cast<W*>(b.P);
+    const int R = b.R;
+    // ---- 1. V^T X per unit ----
+    for (int u = warp; u < b.nunits; u += nw) {
+      const int4 un = b.units[u];
+      const NodeDev& nd = b.nodes[un.x];
+      auto unit = [&](auto tc) {
+        constexpr int TIER = decltype(tc)::value;
+        constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+        for (int c = 0; c < nd.rV; ++c) {
+          W acc[RB];
+#pragma unroll
+          for (int j = 0; j < RB; ++j) acc[j] = (W)0;
+          for (int l = un.y; l < un.z; ++l) {
+            const LeafDev& lf = b.leaves[l];
+            const int lm = lf.m, lrow0 = lf.row0;
+            const uint8_t* col = b.pool + nd.offV + ((int64_t)c * nd.pm + (lf.prow0 - nd.prow0)) * eb;
+            constexpr int kU = batch_unroll<RB>();
+#pragma unroll kU
+            for (int r = lane; r < lm; r += 32) {
+              const W v = ldg_fmt<W, TIER>(col + (int64_t)r * eb);
+              W xv[RB];
+              ld_xrow<W, RB>(X + (int64_t)(lrow0 + r) * b.ldx, R, xv);
+#pragma unroll
+              for (int j = 0; j < RB; ++j) acc[j] = fma(v, xv[j], acc[j]);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < RB; ++j) {
+            if (j >= R) break;
+            const W s = warp_sum(acc[j]);
+            if (lane == 0) P[(int64_t)(un.w + c) * R + j] = s;
+          }
+        }
+      };
+      with_format(nd.tierV, unit);
+    }
+    __syncthreads();
+    // ---- 2. Y_q = scales x (sum of the unit partials in order) ----
+    for (int q = warp; q < b.nnodes; q += nw) {
+      const NodeDev& nd = b.nodes[q];
+      const W sc = (W)(nd.invsV * b.nodes[q ^ 1].invsU);
+      const int u0 = b.node_u[q], u1 = b.node_u[q + 1];
+      for (int e2 = lane; e2 < nd.rV * R; e2 += 32) {
+        const int c = e2 / R, j = e2 - c * R;
+        W s = (W)0;
+        for (int u = u0; u < u1; ++u) s += P[(int64_t)(b.units[u].w + c) * R + j];
+        Y[(int64_t)(b.yoff[q] + c) * R + j] = s * sc;
+      }
+    }
+    __syncthreads();
+    // ---- 3. B rows = D X + U Y, warp per tile, lane = row ----
+    W* B = reinterpret_cast<W*>(b.B);
+    for (int t = warp; t < b.ntiles; t += nw) {
+      const P2Tile& tq = b.tiles[t];
+      const int r = lane;
+      W acc[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) acc[j] = (W)0;
+      const uint8_t* d2 = b.pool + tq.d2off + (int64_t)r * 16;
+      const int nchunk = (tq.m + G16 - 1) / G16;
+      for (int qc = 0; qc < nchunk; ++qc) {
+        W d[G16];
+        if constexpr (sizeof(W) == 4) {
+          const float4 d4 = __ldg(reinterpret_cast<const float4*>(d2 + (int64_t)qc * kTileRows * 16));
+          d[0] = d4.x;
+          d[1] = d4.y;
+          d[2] = d4.z;
+          d[3] = d4.w;
+        } else {
+          const double2 dd = __ldg(reinterpret_cast<const double2*>(d2 + (int64_t)qc * kTileRows * 16));
+          d[0] = dd.x;
+          d[1] = dd.y;
+        }
+#pragma unroll
+        for (int g = 0; g < G16; ++g) {
+          const int cc = qc * G16 + g;
+          if (cc >= tq.m) break;
+          W xv[RB];
+          ld_xrow<W, RB>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
+#pragma unroll
+          for (int j = 0; j < RB; ++j) acc[j] = fma(d[g], xv[j], acc[j]);
+        }
+      }
+      const uint8_t* hdr = b.pool + tq.off;
+      for (int k = 1; k <= b.depth; ++k) {
+        const uint2 hw = *reinterpret_cast<const uint2*>(hdr + 8 * (k - 1));
+        const int ru = (int)(hw.y & 0xffffu), tier = (int)(hw.y >> 16);
+        if (ru == 0) continue;
+        const int sib = node_index(k, (tq.leaf >> (b.depth - k)) ^ 1);
+        const W* yb = Y + (int64_t)b.yoff[sib] * R;
+        const uint8_t* ucol = hdr + tq.hbytes + hw.x;
+        auto level = [&](auto tc) {
+          constexpr int TIER = decltype(tc)::value;
+          constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+          for (int c = 0; c < ru; ++c) {
+            const W uv = ldg_fmt<W, TIER>(ucol + ((int64_t)c * kTileRows + r) * eb);
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+              if (j < R) acc[j] = fma(uv, yb[c * R + j], acc[j]);
+          }
+        };
+        with_format(tier, level);
+      }
+      if (r < tq.rows) {
+        W* brow = B + (int64_t)(tq.row0 + r) * b.ldb;
+#pragma unroll
+        for (int j = 0; j < RB; ++j)
+          if (j < R) brow[j] = acc[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename W>
+cudaError_t launch_batch_w(int rb, int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
+                           cudaStream_t s) {
+  switch (rb) {
+    case 1: batch_kernel<W, 1><<<grid, threads, 0, s>>>(items, first, list); break;
+    case 2: batch_kernel<W, 2><<<grid, threads, 0, s>>>(items, first, list); break;
+    case 4: batch_kernel<W, 4><<<grid, threads, 0, s>>>(items, first, list); break;
+    case 8: batch_kernel<W, 8><<<grid, threads, 0, s>>>(items, first, list); break;
+    default: batch_kernel<W, 16><<<grid, threads, 0, s>>>(items, first, list); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace hodlr
+
+using namespace hodlr;
+
+struct hodlr_batch_s {
+  int count = 0, work = HODLR_FP32, rb = 1, grid = 1, threads = 256, device = 0;
+  BItem* d_items = nullptr;
+  int32_t* d_first = nullptr;
+  int32_t* d_list = nullptr;
+  uint8_t* d_meta = nullptr;   // units, node_u, yoff of every item
+  void* d_scratch = nullptr;   // Y and P of every item
+  ~hodlr_batch_s() {
+    cudaFree(d_items);
+    cudaFree(d_first);
+    cudaFree(d_list);
+    cudaFree(d_meta);
+    cudaFree(d_scratch);
+  }
+};
+
+extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, const int32_t* nrhs, const void* const* X,
+                                           const int64_t* ldx, void* const* B, const int64_t* ldb, int32_t xb_prec,
+                                           hodlr_batch_t* out) {
+  if (!out) return set_error(HODLR_EINVAL, "null out");
+  *out = nullptr;
+  if (count < 1 || !hs || !nrhs || !X || !ldx || !B || !ldb) return set_error(HODLR_EINVAL, "bad batch arguments");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
+  if (xb_prec != HODLR_FP32 && xb_prec != HODLR_FP64) return set_error(HODLR_EINVAL, "X/B precision must be fp32 or fp64");
+  const int es = prec_bytes(xb_prec);
+  int rmax = 1;
+  for (int i = 0; i < count; ++i) {
+    const hodlr_t h = hs[i];
+    if (!h) return set_error(HODLR_EINVAL, "null handle in the batch");
+    if (h->device != dev) return set_error(HODLR_EINVAL, "a handle lives on another device than the current one");
+    if (h->work != xb_prec) return set_error(HODLR_EINVAL, "X/B type must equal every matrix's working precision");
+    if (nrhs[i] < 1 || nrhs[i] > kBatchMaxCols) return set_error(HODLR_EINVAL, "nrhs must be in [1, 16]");
+    if (!X[i] || !B[i] || ldx[i] < nrhs[i] || ldb[i] < nrhs[i]) return set_error(HODLR_EINVAL, "bad X/B of an item");
+    rmax = std::max(rmax, (int)nrhs[i]);
+  }
+  hodlr_batch_s* bt = new hodlr_batch_s();
+  bt->count = count;
+  bt->work = xb_prec;
+  bt->device = dev;
+  bt->rb = rmax <= 1 ? 1 : rmax <= 2 ? 2 : rmax <= 4 ? 4 : rmax <= 8 ? 8 : 16;
+  // work lists: units, node_u, yoff (int32 words) of every item, scratch rows
+  std::vector<int32_t> meta;
+  std::vector<size_t> meta_units(count), meta_nodeu(count), meta_yoff(count);
+  std::vector<int64_t> y_off(count), p_off(count);
+  std::vector<BItem> items(count);
+  std::vector<int> nunits(count);
+  int64_t scratch = 0;
+  std::vector<double> cost(count);
+  for (int i = 0; i < count; ++i) {
+    const hodlr_t h = hs[i];
+    const int depth = h->depth, nnodes = (int)h->nodes.size();
+    std::vector<int4> units;
+    std::vector<int32_t> node_u(nnodes + 1, 0), yoff(std::max(nnodes, 1), 0);
+    int poff = 0, yrows = 0;
+    for (int k = 1; k <= depth; ++k) {
+      const int span = 1 << (depth - k);
+      for (int j = 0; j < (1 << k); ++j) {
+        const int q = node_index(k, j);
+        node_u[q] = (int)units.size();
+        yoff[q] = yrows;
+        yrows += h->nodes[q].rV;
+        if (h->nodes[q].rV == 0) continue;
+        for (int l0 = j * span; l0 < (j + 1) * span; l0 += kLeavesPerUnit) {
+          const int l1 = std::min(l0 + kLeavesPerUnit, (j + 1) * span);
+          units.push_back(make_int4(q, l0, l1, poff));
+          poff += h->nodes[q].rV;
+        }
+      }
+    }
+    node_u[nnodes] = (int)units.size();   // nodes were visited in index order
+    nunits[i] = (int)units.size();
+    // align each section to 16 bytes
+    while (meta.size() % 4) meta.push_back(0);
+    meta_units[i] = meta.size();
+    for (const int4& u : units) {
+      meta.push_back(u.x);
+      meta.push_back(u.y);
+      meta.push_back(u.z);
+      meta.push_back(u.w);
+    }
+    meta_nodeu[i] = meta.size();
+    meta.insert(meta.end(), node_u.begin(), node_u.end());
+    meta_yoff[i] = meta.size();
+    meta.insert(meta.end(), yoff.begin(), yoff.end());
+    y_off[i] = scratch;
+    scratch += (int64_t)std::max(yrows, 1) * nrhs[i];
+    p_off[i] = scratch;
+    scratch += (int64_t)std::max(poff, 1) * nrhs[i];
+    BItem& it = items[i];
+    memset(&it, 0, sizeof(it));
+    it.pool = h->d_pool;
+    it.nodes = h->d_nodes;
+    it.leaves = h->d_leaves;
+    it.tiles = h->d_p2;
+    it.X = X[i];
+    it.B = B[i];
+    it.ldx = ldx[i];
+    it.ldb = ldb[i];
+    it.depth = depth;
+    it.R = nrhs[i];
+    it.nnodes = nnodes;
+    it.nunits = nunits[i];
+    it.ntiles = (int)h->p2.size();
+    cost[i] = (double)(h->info.leaf_bytes + h->info.factor_bytes) + 2.0 * h->n * nrhs[i] * es;
+  }
+  e = cudaMalloc(&bt->d_meta, std::max<size_t>(meta.size(), 4) * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&bt->d_scratch, (size_t)std::max<int64_t>(scratch, 1) * es);
+  if (e == cudaSuccess) e = cudaMalloc(&bt->d_items, sizeof(BItem) * count);
+  int G = 1;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&G, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete bt;
+    return set_error(HODLR_ENOMEM, "batch work list");
+  }
+  G = std::max(1, std::min(G, count));
+  bt->grid = G;
+  const int32_t* dm = reinterpret_cast<const int32_t*>(bt->d_meta);
+  for (int i = 0; i < count; ++i) {
+    items[i].units = reinterpret_cast<const int4*>(dm + meta_units[i]);
+    items[i].node_u = dm + meta_nodeu[i];
+    items[i].yoff = dm + meta_yoff[i];
+    items[i].Y = (uint8_t*)bt->d_scratch + (size_t)y_off[i] * es;
+    items[i].P = (uint8_t*)bt->d_scratch + (size_t)p_off[i] * es;
+  }
+  // longest first onto the least-loaded CTA (deterministic ties: lower index)
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost[a] > cost[c]; });
+  using Load = std::pair<double, int>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> pq;
+  for (int c = 0; c < G; ++c) pq.push({0.0, c});
+  std::vector<std::vector<int>> per(G);
+  for (int i : order) {
+    Load l = pq.top();
+    pq.pop();
+    per[l.second].push_back(i);
+    pq.push({l.first + cost[i], l.second});
+  }
+  std::vector<int32_t> first(G + 1, 0), list;
+  for (int c = 0; c < G; ++c) {
+    first[c] = (int)list.size();
+    list.insert(list.end(), per[c].begin(), per[c].end());
+  }
+  first[G] = (int)list.size();
+  e = cudaMalloc(&bt->d_first, sizeof(int32_t) * (G + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&bt->d_list, sizeof(int32_t) * count);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->d_meta, meta.data(), meta.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->d_items, items.data(), sizeof(BItem) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->d_first, first.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->d_list, list.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    delete bt;
+    return set_cuda_error(e, "hodlr_batch_create");
+  }
+  *out = bt;
+  return HODLR_OK;
+}
+
+extern "C" hodlr_status hodlr_batch_run(hodlr_batch_t b, int32_t threads, void* stream) {
+  if (!b) return set_error(HODLR_EINVAL, "null batch");
+  if (threads == 0) threads = b->threads;
+  if (threads != 128 && threads != 256 && threads != 512) return set_error(HODLR_EINVAL, "threads must be 128, 256 or 512");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = b->work == HODLR_FP64
+                      ? launch_batch_w<double>(b->rb, b->grid, threads, b->d_items, b->d_first, b->d_list, s)
+                      : launch_batch_w<float>(b->rb, b->grid, threads, b->d_items, b->d_first, b->d_list, s);
+  return e == cudaSuccess ? HODLR_OK : set_cuda_error(e, "hodlr_batch_run");
+}
+
+extern "C" hodlr_status hodlr_batch_tune(hodlr_batch_t b, void* stream, int32_t* best_threads, float* best_ms) {
+  if (!b) return set_error(HODLR_EINVAL, "null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return set_error(HODLR_ECUDA, "hodlr_batch_tune: events");
+  }
+  int best = b->threads;
+  float bms = 1e30f;
+  hodlr_status st = HODLR_OK;
+  for (int th : {128, 256, 512}) {
+    for (int w = 0; w < 2 && st == HODLR_OK; ++w) st = hodlr_batch_run(b, th, stream);
+    float tot = 0.0f;
+    for (int rep = 0; rep < 5 && st == HODLR_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = hodlr_batch_run(b, th, stream);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(HODLR_ECUDA, "hodlr_batch_tune");
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (st != HODLR_OK) break;
+    if (tot / 5 < bms) {
+      bms = tot / 5;
+      best = th;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HODLR_OK) return st;
+  b->threads = best;
+  if (best_threads) *best_threads = best;
+  if (best_ms) *best_ms = bms;
+  return HODLR_OK;
+}
+
+extern "C" void hodlr_batch_destroy(hodlr_batch_t b) { delete b; }

@@ -116,7 +116,9 @@ struct P2Tile {
   int32_t nq;                     // U columns (sum of the ancestors' ranks)
   int32_t yrow;                   // first row of the leaf's block in the gathered Y
   int32_t ubytes;                 // U bytes after the header (multiple of 16)
+  int32_t leaf;                   // the tile's leaf
 };
+static_assert(sizeof(P2Tile) % 8 == 0, "P2Tile records are copied whole (8-byte aligned)");
 
 // Tensor-core products (fp32 work, many right-hand sides).  A leaf group is
 // up to 128 consecutive rows of one leaf, i.e. up to four product tiles:

@@ -290,6 +290,59 @@ class HodlrMatrix:
             pass
 
 
+class HodlrBatch:
+    """A planned batch of products B_i = H_i X_i in one launch
+    (hodlr_batch_create / _run / _tune / _destroy).  Keeps the handles and
+    the X/B tensors alive for its own lifetime."""
+
+    def __init__(self, mats: Sequence["HodlrMatrix"], Xs: Sequence[torch.Tensor], Bs: Sequence[torch.Tensor]):
+        if not (len(mats) == len(Xs) == len(Bs)) or not mats:
+            raise ValueError("one X and one B per matrix")
+        work = mats[0].work
+        self._keep = (list(mats), list(Xs), list(Bs))
+        cnt = len(mats)
+        hs = (ctypes.c_void_p * cnt)(*[m._h for m in mats])
+        nr = (ctypes.c_int32 * cnt)()
+        xp = (ctypes.c_void_p * cnt)()
+        bp = (ctypes.c_void_p * cnt)()
+        lx = (ctypes.c_int64 * cnt)()
+        lb = (ctypes.c_int64 * cnt)()
+        for i, (m, X, B) in enumerate(zip(mats, Xs, Bs)):
+            if X.dim() != 2 or B.dim() != 2 or X.stride(1) != 1 or B.stride(1) != 1 or X.shape != B.shape:
+                raise ValueError("X and B must be (n, R) tensors with unit column stride")
+            if X.dtype != m.dtype or B.dtype != m.dtype or not X.is_cuda or not B.is_cuda or X.shape[0] != m.n:
+                raise ValueError("X and B must be CUDA tensors of the matrix's working dtype with n rows")
+            nr[i] = X.shape[1]
+            xp[i] = X.data_ptr()
+            bp[i] = B.data_ptr()
+            lx[i] = X.stride(0)
+            lb[i] = B.stride(0)
+        self._b = ctypes.c_void_p()
+        check(load().hodlr_batch_create(cnt, hs, nr, xp, lx, bp, lb, PREC[work], ctypes.byref(self._b)),
+              "hodlr_batch_create")
+
+    def run(self, threads: int = 0, stream=None):
+        check(load().hodlr_batch_run(self._b, int(threads), _stream_ptr(stream)), "hodlr_batch_run")
+
+    def tune(self, stream=None):
+        th = ctypes.c_int32()
+        ms = ctypes.c_float()
+        check(load().hodlr_batch_tune(self._b, _stream_ptr(stream), ctypes.byref(th), ctypes.byref(ms)),
+              "hodlr_batch_tune")
+        return th.value, ms.value
+
+    def close(self):
+        if self._b:
+            load().hodlr_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dense_kernel_matvec(points: torch.Tensor, kind: int, X: torch.Tensor, c: float = 0.0,
                         len2: float = 1.0, diag: float = 0.0, rows: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:
