@@ -148,6 +148,12 @@ typedef struct {
   int32_t sketch;      /* first sketch size per block (0 -> 16) */
   int32_t max_sketch;  /* largest sketch size, <= 64 (0 -> 64) */
   uint64_t seed;       /* seed of the Gaussian test matrix */
+  const int32_t* node_sketch;  /* NULL, or host int32[2^(depth+1) - 2]: the
+                                  first sketch of block (k, i) at node
+                                  2^k - 2 + i (clamped to [1, max_sketch]),
+                                  e.g. from a rank predictor; a block whose
+                                  sketch falls short is redone with twice its
+                                  sketch as always */
 } hodlr_build_opts;
 
 /* hodlr_build -- construct the adaptive-precision HODLR matrix of a kernel
@@ -172,6 +178,13 @@ typedef struct {
 hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel* kernel,
                          const double* points, const hodlr_opts* opts,
                          const hodlr_build_opts* bopts, void* stream, hodlr_t* out);
+
+/* hodlr_build_stats -- how the last hodlr_build of this handle went:
+ * rounds of the range finder, blocks redone with a larger sketch (summed over
+ * the rounds after the first), and the sum over rounds of the sketch columns
+ * of the blocks in the round.  Any output may be NULL; zeros for a handle
+ * from hodlr_import or hodlr_load. */
+hodlr_status hodlr_build_stats(hodlr_t h, int32_t* rounds, int32_t* redone, int64_t* sketch_cols);
 
 /* hodlr_export -- read the stored generators back, decoded to fp64 (the
  * values Algorithm 3.3 multiplies by: stored / scale).  Same layouts as
@@ -291,6 +304,50 @@ hodlr_status hodlr_info(hodlr_t h, hodlr_info_t* out);
 /* hodlr_block_tiers -- per node (layout as ranks in hodlr_import): the storage
  * format (hodlr_prec) and rank of block (i, i^1).  Either output may be NULL. */
 hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks);
+
+/* ---- block-rank predictor ---------------------------------------------------- */
+/* A 11-64-64-64-1 multilayer perceptron (relu hidden layers, fp16 weights,
+ * fp32 arithmetic) that predicts y = log2(rank + 1) of an off-diagonal block
+ * from cheap features, to size each block's first sketch in hodlr_build
+ * (hodlr_build_opts.node_sketch).  The paper has no learned component; the
+ * adaptive rule still decides every rank.  Parameter vector (P =
+ * hodlr_mlp_num_params() = 9153 values): W1 (64 x 11, row-major), b1 (64),
+ * W2 (64 x 64), b2, W3 (64 x 64), b3, W4 (1 x 64), b4 (1).  All arrays are
+ * device arrays; calls are enqueued on `stream` unless stated. */
+int32_t hodlr_mlp_num_params(void);
+
+/* hodlr_mlp_features -- the 11 features of every off-diagonal block of the
+ * kernel matrix of `points` (device, (n, dim) fp64, tree order) with depth
+ * levels, in node order (feat: fp32 [2^(depth+1) - 2][11]): k / 12,
+ * log2(m) / 20, log10(eps) / 10, and log10 of eight row norms of the block
+ * (rows (2j + 1) m / 16, all columns; entries generated in registers) over
+ * the largest of them, / 10.  Synchronous.  Errors: HODLR_EINVAL,
+ * HODLR_ENOMEM, HODLR_ECUDA. */
+hodlr_status hodlr_mlp_features(const hodlr_kernel* kernel, const double* points, int32_t n,
+                                int32_t depth, double eps, float* feat, void* stream);
+
+/* hodlr_mlp_forward -- y[s] for S samples X (fp32 [S][11]) with the fp16
+ * parameters w16; act (fp32 [S][192], or NULL) receives the pre-activations
+ * of the three hidden layers for hodlr_mlp_backward. */
+hodlr_status hodlr_mlp_forward(const uint16_t* w16, int32_t S, const float* X, float* y,
+                               float* act, void* stream);
+
+/* hodlr_mlp_loss -- mean squared error of y against targets t (written to
+ * *loss, device) and dy = 2 (y - t) / S. */
+hodlr_status hodlr_mlp_loss(int32_t S, const float* y, const float* t, float* dy, float* loss,
+                            void* stream);
+
+/* hodlr_mlp_backward -- grad (fp32 [P]) = dL/dparameters for the samples of
+ * the last forward (X, act) and dy, by the chain rule; work: fp32 [S][192]
+ * scratch.  Every sum runs over the samples in order (reproducible). */
+hodlr_status hodlr_mlp_backward(const uint16_t* w16, int32_t S, const float* X, const float* act,
+                                const float* dy, float* grad, float* work, void* stream);
+
+/* hodlr_mlp_adam -- one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step
+ * counts from 1) on the fp32 master parameters w32 with moments m, v; w16
+ * receives the updated parameters rounded to fp16. */
+hodlr_status hodlr_mlp_adam(float* w32, uint16_t* w16, float* m, float* v, const float* grad,
+                            int32_t step, float lr, void* stream);
 
 /* ---- batched products ------------------------------------------------------ */
 

@@ -18,6 +18,9 @@ Plain, slow and written to be checked by eye against the paper:
 * ``matvec``   HODLR_MATVEC (Algorithm 3.3) and the dense assembly of H-hat.
 * ``bounds``   gamma_n and the error bounds of Thm 3.1, eq. (3.5), Thm 3.5.
 * ``lu``       HODLR_LU (Algorithm 3.4) and the triangular solves.
+* ``mlp``      the block-rank predictor that sizes the construction's first
+               sketch (affine + relu layers, chain-rule gradient, Adam); the
+               paper has no learned component, these are plain definitions.
 
 Parity status per function is stated in each module header.
 """

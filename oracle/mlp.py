@@ -119,10 +119,11 @@ def init_params(seed: int) -> np.ndarray:
     return np.concatenate(parts)
 
 
-def sketch_from_prediction(y: np.ndarray, smax: int = 64, over: int = 8) -> np.ndarray:
+def sketch_from_prediction(y: np.ndarray, smin: int = 16, smax: int = 64, over: int = 8) -> np.ndarray:
     """First sketch size per block from the predicted log2(rank + 1): the
     predicted rank plus `over` columns, rounded up to a multiple of 8, in
-    [8, smax]."""
+    [smin, smax] (smin = the construction's default first sketch: the
+    prediction only ever raises it)."""
     r = np.maximum(np.exp2(np.asarray(y, dtype=np.float64)) - 1.0, 0.0)
     s = np.ceil((r + over) / 8.0) * 8.0
-    return np.clip(s, 8, smax).astype(np.int32)
+    return np.clip(s, smin, smax).astype(np.int32)

@@ -46,7 +46,7 @@ class Kernel(ctypes.Structure):
 
 class BuildOpts(ctypes.Structure):
     _fields_ = [("sketch", ctypes.c_int32), ("max_sketch", ctypes.c_int32),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("node_sketch", ctypes.POINTER(ctypes.c_int32))]
 
 
 class SolveStats(ctypes.Structure):
@@ -79,6 +79,7 @@ SIGNATURES = {
     "hodlr_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "hodlr_block_tiers": (ctypes.c_int, [_P, _I32P, _I32P]),
     "hodlr_node_sizes": (ctypes.c_int, [_P, _I32P, _I32P]),
+    "hodlr_build_stats": (ctypes.c_int, [_P, _I32P, _I32P, ctypes.POINTER(ctypes.c_int64)]),
     "hodlr_dense_kernel_matvec": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_int32, _P, ctypes.c_int32, _P,
@@ -94,6 +95,13 @@ SIGNATURES = {
     "hodlr_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "hodlr_batch_tune": (ctypes.c_int, [_P, _P, _I32P, ctypes.POINTER(ctypes.c_float)]),
     "hodlr_batch_destroy": (None, [_P]),
+    "hodlr_mlp_num_params": (ctypes.c_int32, []),
+    "hodlr_mlp_features": (ctypes.c_int, [ctypes.POINTER(Kernel), _P, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_double, _P, _P]),
+    "hodlr_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "hodlr_mlp_loss": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "hodlr_mlp_backward": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
+    "hodlr_mlp_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_float, _P]),
     "hodlr_destroy": (None, [_P]),
     "hodlr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hodlr_last_error": (ctypes.c_char_p, []),

@@ -1403,6 +1403,14 @@ hodlr_status hodlr_block_tiers(hodlr_t h, int32_t* tiers, int32_t* ranks) {
   return HODLR_OK;
 }
 
+hodlr_status hodlr_build_stats(hodlr_t h, int32_t* rounds, int32_t* redone, int64_t* sketch_cols) {
+  if (!h) return fail(HODLR_EINVAL, "null handle");
+  if (rounds) *rounds = h->build_rounds;
+  if (redone) *redone = h->build_redone;
+  if (sketch_cols) *sketch_cols = h->build_sketch_cols;
+  return HODLR_OK;
+}
+
 hodlr_status hodlr_node_sizes(hodlr_t h, int32_t* row0, int32_t* m) {
   if (!h) return fail(HODLR_EINVAL, "null handle");
   for (size_t q = 0; q < h->nodes.size(); ++q) {

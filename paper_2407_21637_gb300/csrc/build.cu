@@ -683,23 +683,31 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
       b.q = node_index(k, i);
       pending.push_back(b);
     }
-  int s = s0;
+  // every block's current sketch: the node's own first sketch when given
+  std::vector<int> sk(nnodes, s0);
+  if (bopts && bopts->node_sketch)
+    for (int q = 0; q < nnodes; ++q) sk[q] = std::max(1, std::min(bopts->node_sketch[q], smax));
+  int nrounds = 0, redone = 0;
+  int64_t sketch_cols = 0;
   bool accuracy_short = false;
   double worst_ratio = 0.0;
   std::string worst_msg;
   while (!pending.empty()) {
     auto R = std::make_unique<Round>();
     for (BBlock b : pending) {
-      b.s = std::min(s, std::min(b.m, b.mc));
+      b.s = std::min(sk[b.q], std::min(b.m, b.mc));
+      sketch_cols += b.s;
       R->blocks.push_back(b);
     }
+    if (nrounds++ > 0) redone += (int)pending.size();
     hodlr_status stt = run_round(*R, K, d_om, opts->eps, mem, st);
     if (stt != HODLR_OK) return stt;
     pending.clear();
     const int ri = (int)rounds.size();
     for (int bi = 0; bi < (int)R->blocks.size(); ++bi) {
       const BBlock& b = R->blocks[bi];
-      if (b.retry && s < smax) {
+      if (b.retry && b.s < std::min(smax, std::min(b.m, b.mc))) {
+        sk[b.q] = std::min(2 * sk[b.q], smax);
         pending.push_back(b);
         continue;
       }
@@ -720,7 +728,6 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
       block_norm2[b.q] = b.norm2;
     }
     rounds.push_back(std::move(R));
-    s = std::min(2 * s, smax);
   }
 
   // layout with the final ranks, then U = Q W_r and V = Q2 (Z S)_r into the staging
@@ -772,6 +779,9 @@ extern "C" hodlr_status hodlr_build(int32_t n, int32_t depth, const hodlr_kernel
   stt = finish_from_staging(h, d_stage, block_norm2.data(), nullptr, opts, st);
   if (stt != HODLR_OK) return stt;
   h->build_accuracy_short = accuracy_short;
+  h->build_rounds = nrounds;
+  h->build_redone = redone;
+  h->build_sketch_cols = sketch_cols;
   *out = guard.release();
   if (accuracy_short)
     return set_error(HODLR_EACCURACY, "a block needed a sketch larger than max_sketch (its rank is capped); worst: " + worst_msg);

@@ -47,6 +47,8 @@ struct hodlr_s {
   hodlr_info_t info{};
   int build_sketch_max = 0;          // largest sketch hodlr_build used
   bool build_accuracy_short = false;  // some block hit the sketch cap
+  int build_rounds = 0, build_redone = 0;   // range-finder rounds, blocks redone
+  int64_t build_sketch_cols = 0;      // sum over rounds of the blocks' sketch columns
   uint8_t* d_pool = nullptr;
   size_t pool_bytes = 0;
   NodeDev* d_nodes = nullptr;

@@ -77,7 +77,8 @@ class HodlrMatrix:
               len2: float = 1.0, diag: float = 0.0, work: str = "fp32",
               tiers: Sequence[str] = ("fp64", "fp32", "bf16", "fp16", "e4m3"),
               per_block: bool = False, max_nrhs: int = 64, sketch: int = 0, max_sketch: int = 0,
-              seed: int = 0, stream=None, allow_short: bool = False) -> "HodlrMatrix":
+              seed: int = 0, stream=None, allow_short: bool = False,
+              node_sketch: Sequence[int] | None = None) -> "HodlrMatrix":
         """hodlr_build: compress the kernel matrix of ``points`` ((n, dim) fp64
         CUDA tensor, tree order) on the GPU (Algorithm 3.2 with a randomized
         range finder) and store it in the adaptive-precision format."""
@@ -94,6 +95,12 @@ class HodlrMatrix:
         opts = Opts(eps=float(eps), work=PREC[work], tier_mask=mask, per_block=int(per_block),
                     max_nrhs=int(max_nrhs))
         bo = BuildOpts(sketch=int(sketch), max_sketch=int(max_sketch), seed=int(seed))
+        if node_sketch is not None:
+            ns = np.ascontiguousarray(np.asarray(node_sketch, dtype=np.int32))
+            if ns.size != (1 << (depth + 1)) - 2:
+                raise ValueError("node_sketch needs one entry per node (2^(depth+1) - 2)")
+            bo.node_sketch = ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            bo._keep = ns   # the array must outlive the call
         h = ctypes.c_void_p()
         st = lib.hodlr_build(n, depth, ctypes.byref(kern), ctypes.c_void_p(pts.data_ptr()),
                              ctypes.byref(opts), ctypes.byref(bo), _stream_ptr(stream), ctypes.byref(h))
@@ -182,6 +189,14 @@ class HodlrMatrix:
         r = (ctypes.c_int32 * max(nn, 1))()
         check(load().hodlr_block_tiers(self._h, t, r), "hodlr_block_tiers")
         return [PREC_NAME[t[q]] for q in range(nn)], [r[q] for q in range(nn)]
+
+    def build_stats(self):
+        """hodlr_build_stats: (rounds, blocks redone, sketch columns summed over rounds)."""
+        r, d = ctypes.c_int32(), ctypes.c_int32()
+        c = ctypes.c_int64()
+        check(load().hodlr_build_stats(self._h, ctypes.byref(r), ctypes.byref(d), ctypes.byref(c)),
+              "hodlr_build_stats")
+        return r.value, d.value, c.value
 
     def node_sizes(self):
         """The cluster tree from the library (hodlr_node_sizes): levels[k][i] =
@@ -288,6 +303,104 @@ class HodlrMatrix:
             self.close()
         except Exception:
             pass
+
+
+class RankPredictor:
+    """The block-rank predictor (hodlr_mlp_*): fp32 master parameters and
+    their fp16 copy on the device, Adam moments, features of a kernel
+    matrix's blocks, training and first-sketch sizes for hodlr_build."""
+
+    N_IN = 11
+
+    def __init__(self, params: np.ndarray | None = None, seed: int = 0, device=None):
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.P = int(load().hodlr_mlp_num_params())
+        if params is None:
+            params = self.init_params(seed)
+        p = np.asarray(params, dtype=np.float32)
+        if p.size != self.P:
+            raise ValueError(f"expected {self.P} parameters")
+        self.w32 = torch.from_numpy(p.copy()).to(dev)
+        self.w16 = self.w32.half()
+        self.m = torch.zeros_like(self.w32)
+        self.v = torch.zeros_like(self.w32)
+        self.step = 0
+        self.device = dev
+
+    def init_params(self, seed: int) -> np.ndarray:
+        """He-style initialization of the layout: weights ~ N(0, 2 / fan_in), biases 0."""
+        rng = np.random.default_rng(seed)
+        parts = []
+        for shape in ((64, 11), (64,), (64, 64), (64,), (64, 64), (64,), (1, 64), (1,)):
+            parts.append(rng.standard_normal(shape).ravel() * np.sqrt(2.0 / shape[1]) if len(shape) == 2
+                         else np.zeros(shape))
+        return np.concatenate(parts)
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+
+    def features(self, points: torch.Tensor, kind: int, depth: int, eps: float, c: float = 0.0,
+                 len2: float = 1.0, diag: float = 0.0, stream=None) -> torch.Tensor:
+        pts = (points if points.dim() == 2 else points.view(-1, 1)).contiguous()
+        n, dim = pts.shape
+        feat = torch.empty(((1 << (depth + 1)) - 2, self.N_IN), dtype=torch.float32, device=pts.device)
+        kern = Kernel(kind=int(kind), dim=int(dim), c=float(c), len2=float(len2), diag=float(diag))
+        check(load().hodlr_mlp_features(ctypes.byref(kern), self._p(pts), n, depth, float(eps), self._p(feat),
+                                        _stream_ptr(stream)), "hodlr_mlp_features")
+        return feat
+
+    def forward(self, X: torch.Tensor, act: bool = False, stream=None):
+        X = X.contiguous()
+        S = X.shape[0]
+        y = torch.empty(S, dtype=torch.float32, device=X.device)
+        a = torch.empty((S, 192), dtype=torch.float32, device=X.device) if act else None
+        check(load().hodlr_mlp_forward(self._p(self.w16), S, self._p(X), self._p(y), self._p(a), _stream_ptr(stream)),
+              "hodlr_mlp_forward")
+        return (y, a) if act else y
+
+    def gradient(self, X: torch.Tensor, t: torch.Tensor, stream=None):
+        """(loss, grad) of the mean squared error over the samples."""
+        X = X.contiguous()
+        t = t.contiguous().float()
+        S = X.shape[0]
+        y, a = self.forward(X, act=True, stream=stream)
+        dy = torch.empty_like(y)
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        lib = load()
+        check(lib.hodlr_mlp_loss(S, self._p(y), self._p(t), self._p(dy), self._p(loss), _stream_ptr(stream)),
+              "hodlr_mlp_loss")
+        grad = torch.empty_like(self.w32)
+        work = torch.empty((S, 192), dtype=torch.float32, device=X.device)
+        check(lib.hodlr_mlp_backward(self._p(self.w16), S, self._p(X), self._p(a), self._p(dy), self._p(grad),
+                                     self._p(work), _stream_ptr(stream)), "hodlr_mlp_backward")
+        return loss, grad
+
+    def adam(self, grad: torch.Tensor, lr: float, stream=None):
+        self.step += 1
+        check(load().hodlr_mlp_adam(self._p(self.w32), self._p(self.w16), self._p(self.m), self._p(self.v),
+                                    self._p(grad), self.step, float(lr), _stream_ptr(stream)), "hodlr_mlp_adam")
+
+    def train(self, X: torch.Tensor, t: torch.Tensor, epochs: int = 200, lr: float = 3e-3, stream=None):
+        """Full-batch Adam; returns the loss before each step (host floats)."""
+        losses = []
+        for _ in range(epochs):
+            loss, grad = self.gradient(X, t, stream=stream)
+            self.adam(grad, lr, stream=stream)
+            losses.append(loss)
+        return [float(v.item()) for v in losses]
+
+    @staticmethod
+    def sketch_sizes(y, smin: int = 16, smax: int = 64, over: int = 8) -> np.ndarray:
+        """First sketch per block: the predicted rank 2^y - 1 plus `over`
+        columns, rounded up to a multiple of 8, in [smin, smax] (smin = the
+        construction's default first sketch, so the prediction only raises
+        it: a round of the range finder costs about the same for any sketch
+        up to 64 columns, while a block whose sketch falls short costs another
+        round)."""
+        y = y.detach().cpu().numpy().astype(np.float64) if isinstance(y, torch.Tensor) else np.asarray(y, np.float64)
+        r = np.maximum(np.exp2(y) - 1.0, 0.0)
+        return np.clip(np.ceil((r + over) / 8.0) * 8.0, smin, smax).astype(np.int32)
 
 
 class HodlrBatch:

@@ -82,8 +82,9 @@ def test_parameters_are_rounded_to_fp16():
 
 
 def test_sketch_from_prediction():
-    y = np.log2(np.array([0.0, 7.0, 15.0, 100.0]) + 1.0)
-    assert P.sketch_from_prediction(y).tolist() == [8, 16, 24, 64]
+    y = np.log2(np.array([0.0, 7.0, 15.0, 20.0, 100.0]) + 1.0)
+    assert P.sketch_from_prediction(y).tolist() == [16, 16, 24, 32, 64]
+    assert P.sketch_from_prediction(y, smin=8).tolist() == [8, 16, 24, 32, 64]
 
 
 def test_planted_wrong_relu_derivative_is_caught(monkeypatch):
