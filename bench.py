@@ -72,7 +72,7 @@ HOST_AHEAD_CYCLES = 400_000   # ~0.2 ms spin before each timed product (host sub
 # on (SHA-256 of those files), else null.
 TRAFFIC_PER_STEP = {
     "stream_kernel": (("hodlr_internal.cuh", "dev_common.cuh", "stream.cu"),
-                      "252a0f8a6f7f474d4e21ccb27e98493f4b0843ebad07550514969f2895a8bae1", 175477248),
+                      "50edc2082aaf061196a63777c5b4631fb4c75dc4d7846889234da8effacc5791", 175134976),
 }
 
 
@@ -479,6 +479,86 @@ def run_batch_block(dev, peak, flush, stream):
             "one_launch_per_item_ms": ms_single, "speedup_over_one_launch_per_item": ms_single / ms_batch}
 
 
+def _predictor_workloads(seed, count, nlo, nhi, eps_lo, eps_hi):
+    """(kind, n, depth, eps, c, len2, diag) draws of the batched workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(nlo), math.log(nhi)))))
+        depth = max(1, math.ceil(math.log2(n / 128)))
+        eps = float(math.exp(rng.uniform(math.log(eps_lo), math.log(eps_hi))))
+        if rng.uniform() < 0.5:
+            out.append((0, n, depth, eps, 1e-3, 1.0, float(n)))
+        else:
+            ell = float(rng.uniform(0.02, 0.2))
+            out.append((1, n, depth, eps, 0.0, ell * ell, 1e-2))
+    return out
+
+
+def run_predictor_block(dev):
+    """The block-rank predictor: trained (full-batch Adam, 400 steps) on the
+    blocks of GPU builds of the LU workload, the headline Gaussian at n = 16384,
+    the 1/(r + 1e-4) kernel at n = 4096 and 8192 and six batched-workload draws;
+    then hodlr_build of eight held-out batched-workload draws (n log-U[8192,
+    32768], eps log-U[1e-10, 1e-7]) with the default first sketch (16, doubled
+    per short block) and with the predicted first sketches: wall time,
+    range-finder rounds and blocks redone."""
+    import torch
+
+    import synth
+    from paper_2407_21637_gb300 import HodlrMatrix, RankPredictor
+    train = [(0, 1024, 4, 1e-8, 1e-3, 1.0, 1024.0), (1, 16384, 6, 1e-6, 0.0, 0.01, 1e-2),
+             (0, 4096, 4, 1e-6, 1e-4, 1.0, 0.0), (0, 8192, 5, 1e-6, 1e-4, 1.0, 0.0)]
+    train += _predictor_workloads(3, 6, 2048, 16384, 1e-10, 1e-3)
+    rp = RankPredictor(seed=1)
+    Xs, ts = [], []
+    t0 = time.perf_counter()
+    for i, (kind, n, depth, eps, c, len2, diag) in enumerate(train):
+        pts = torch.from_numpy(synth.uniform_points_1d(n, i)).to(dev)
+        g = HodlrMatrix.build(pts, kind, depth, eps, c=c, len2=len2, diag=diag, work="fp32", per_block=True,
+                              seed=i, allow_short=True)
+        Xs.append(rp.features(pts, kind, depth, eps, c=c, len2=len2, diag=diag))
+        ts.append(torch.tensor(np.log2(np.asarray(g.block_tiers()[1], dtype=np.float64) + 1.0), dtype=torch.float32))
+        g.close()
+    X, t = torch.cat(Xs), torch.cat(ts).to(dev)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    losses = rp.train(X, t, epochs=400, lr=3e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = []
+    tot = {"default": [0.0, 0, 0], "predicted": [0.0, 0, 0]}
+    for i, (kind, n, depth, eps, c, len2, diag) in enumerate(_predictor_workloads(11, 8, 8192, 32768, 1e-10, 1e-7)):
+        pts = torch.from_numpy(synth.uniform_points_1d(n, 900 + i)).to(dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sk = RankPredictor.sketch_sizes(rp.forward(rp.features(pts, kind, depth, eps, c=c, len2=len2, diag=diag)))
+        t_pred = time.perf_counter() - t0
+        row = {"n": n, "depth": depth, "eps": eps, "kernel": "inv_dist" if kind == 0 else "gauss"}
+        for name, ns in (("default", None), ("predicted", sk)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = HodlrMatrix.build(pts, kind, depth, eps, c=c, len2=len2, diag=diag, work="fp32", per_block=True,
+                                  seed=9, node_sketch=ns, allow_short=True)
+            torch.cuda.synchronize()
+            tb = time.perf_counter() - t0 + (t_pred if ns is not None else 0.0)
+            r, red, _cols = g.build_stats()
+            row[name] = {"build_s": tb, "rounds": r, "redone": red, "max_rank": g.info()["max_rank"]}
+            tot[name][0] += tb
+            tot[name][1] += r
+            tot[name][2] += red
+            g.close()
+        rows.append(row)
+    return {"training": {"samples": int(X.shape[0]), "data_s": t_data, "train_s": t_train,
+                         "loss_first": losses[0], "loss_last": losses[-1]},
+            "held_out": rows,
+            "total_build_s": {k: v[0] for k, v in tot.items()},
+            "total_rounds": {k: v[1] for k, v in tot.items()},
+            "total_redone": {k: v[2] for k, v in tot.items()},
+            "build_time_gain": tot["default"][0] / max(tot["predicted"][0], 1e-9),
+            "note": "predicted build times include the features and the forward pass"}
+
+
 C5_WL = dict(name="inv_dist_2p20", logn=20, eps=1e-6, c=1e-4, seed=5, rhs=64)
 
 
@@ -771,6 +851,7 @@ def run_ours(args, rank, world, dist):
         line["lu_solve"] = run_lu_block(dev, with_cpu=not args.no_cpu)
     if rank == 0 and not args.quick:
         line["batched"] = run_batch_block(dev, peak, flush, stream)
+        line["rank_predictor"] = run_predictor_block(dev)
     if rank == 0 and args.c5:
         line["c5"] = run_c5_block(dev, peak, flush, stream)
     if rank == 0 and not args.no_cpu:

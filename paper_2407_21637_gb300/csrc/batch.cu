@@ -69,9 +69,15 @@ __device__ __forceinline__ void ld_xrow(const W* x, int R, W (&xv)[RB]) {
   for (int j = 0; j < RB; ++j) xv[j] = j < R ? __ldg(x + j) : (W)0;
 }
 
-// Loads of one row step in flight: fewer as the rows get wider.
+// Row steps unrolled in the V^T X units, V columns per pass and leaf-block
+// chunks loaded ahead in the tile pass: more as the rows get narrower (the
+// registers they take grow with RB).
 template <int RB>
-__host__ __device__ constexpr int batch_unroll() { return RB >= 8 ? 1 : RB >= 4 ? 2 : 4; }
+__host__ __device__ constexpr int batch_unroll() { return RB >= 8 ? 1 : 2; }
+template <int RB>
+__host__ __device__ constexpr int batch_cols() { return RB <= 2 ? 8 : RB <= 4 ? 4 : RB <= 8 ? 2 : 1; }
+template <int RB>
+__host__ __device__ constexpr int batch_dq() { return RB <= 4 ? 8 : 4; }
 
 template <typename W, int RB>
 __global__ void __launch_bounds__(512, 1)
@@ -85,36 +91,50 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
     W* Y = reinterpret_cast<W*>(b.Y);
     W* P = reinterpret_cast<W*>(b.P);
     const int R = b.R;
-    // ---- 1. V^T X per unit ----
+    // ---- 1. V^T X per unit: CG columns of V_q at a time (independent
+    //      loads in flight: CG V values and the X row per row step) ----
     for (int u = warp; u < b.nunits; u += nw) {
       const int4 un = b.units[u];
       const NodeDev& nd = b.nodes[un.x];
       auto unit = [&](auto tc) {
         constexpr int TIER = decltype(tc)::value;
         constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
-        for (int c = 0; c < nd.rV; ++c) {
-          W acc[RB];
+        constexpr int CG = batch_cols<RB>();
+        for (int c0 = 0; c0 < nd.rV; c0 += CG) {
+          W acc[CG][RB];
 #pragma unroll
-          for (int j = 0; j < RB; ++j) acc[j] = (W)0;
+          for (int a = 0; a < CG; ++a)
+#pragma unroll
+            for (int j = 0; j < RB; ++j) acc[a][j] = (W)0;
           for (int l = un.y; l < un.z; ++l) {
             const LeafDev& lf = b.leaves[l];
             const int lm = lf.m, lrow0 = lf.row0;
-            const uint8_t* col = b.pool + nd.offV + ((int64_t)c * nd.pm + (lf.prow0 - nd.prow0)) * eb;
+            const uint8_t* col0 = b.pool + nd.offV + ((int64_t)c0 * nd.pm + (lf.prow0 - nd.prow0)) * eb;
+            const int64_t cstride = (int64_t)nd.pm * eb;
             constexpr int kU = batch_unroll<RB>();
 #pragma unroll kU
             for (int r = lane; r < lm; r += 32) {
-              const W v = ldg_fmt<W, TIER>(col + (int64_t)r * eb);
               W xv[RB];
               ld_xrow<W, RB>(X + (int64_t)(lrow0 + r) * b.ldx, R, xv);
 #pragma unroll
-              for (int j = 0; j < RB; ++j) acc[j] = fma(v, xv[j], acc[j]);
+              for (int a = 0; a < CG; ++a) {
+                // columns past the rank read the last column (never stored)
+                const int cc = min(a, nd.rV - 1 - c0);
+                const W v = ldg_fmt<W, TIER>(col0 + cc * cstride + (int64_t)r * eb);
+#pragma unroll
+                for (int j = 0; j < RB; ++j) acc[a][j] = fma(v, xv[j], acc[a][j]);
+              }
             }
           }
 #pragma unroll
-          for (int j = 0; j < RB; ++j) {
-            if (j >= R) break;
-            const W s = warp_sum(acc[j]);
-            if (lane == 0) P[(int64_t)(un.w + c) * R + j] = s;
+          for (int a = 0; a < CG; ++a) {
+            if (c0 + a >= nd.rV) break;
+#pragma unroll
+            for (int j = 0; j < RB; ++j) {
+              if (j >= R) break;
+              const W sm = warp_sum(acc[a][j]);
+              if (lane == 0) P[(int64_t)(un.w + c0 + a) * R + j] = sm;
+            }
           }
         }
       };
@@ -144,27 +164,37 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
       for (int j = 0; j < RB; ++j) acc[j] = (W)0;
       const uint8_t* d2 = b.pool + tq.d2off + (int64_t)r * 16;
       const int nchunk = (tq.m + G16 - 1) / G16;
-      for (int qc = 0; qc < nchunk; ++qc) {
-        W d[G16];
-        if constexpr (sizeof(W) == 4) {
-          const float4 d4 = __ldg(reinterpret_cast<const float4*>(d2 + (int64_t)qc * kTileRows * 16));
-          d[0] = d4.x;
-          d[1] = d4.y;
-          d[2] = d4.z;
-          d[3] = d4.w;
-        } else {
-          const double2 dd = __ldg(reinterpret_cast<const double2*>(d2 + (int64_t)qc * kTileRows * 16));
-          d[0] = dd.x;
-          d[1] = dd.y;
-        }
+      // DQ chunks of the leaf-block row loaded before any is used (16-byte
+      // vectors, consecutive lanes consecutive rows); the X rows are the same
+      // on every lane (one broadcast transaction each)
+      constexpr int DQ = batch_dq<RB>();
+      for (int q0 = 0; q0 < nchunk; q0 += DQ) {
+        uint4 raw[DQ];
 #pragma unroll
-        for (int g = 0; g < G16; ++g) {
-          const int cc = qc * G16 + g;
-          if (cc >= tq.m) break;
-          W xv[RB];
-          ld_xrow<W, RB>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
+        for (int qq = 0; qq < DQ; ++qq)
+          raw[qq] = q0 + qq < nchunk ? __ldg(reinterpret_cast<const uint4*>(d2 + (int64_t)(q0 + qq) * kTileRows * 16))
+                                     : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-          for (int j = 0; j < RB; ++j) acc[j] = fma(d[g], xv[j], acc[j]);
+        for (int qq = 0; qq < DQ; ++qq) {
+          W d[G16];
+          if constexpr (sizeof(W) == 4) {
+            d[0] = __uint_as_float(raw[qq].x);
+            d[1] = __uint_as_float(raw[qq].y);
+            d[2] = __uint_as_float(raw[qq].z);
+            d[3] = __uint_as_float(raw[qq].w);
+          } else {
+            d[0] = __hiloint2double((int)raw[qq].y, (int)raw[qq].x);
+            d[1] = __hiloint2double((int)raw[qq].w, (int)raw[qq].z);
+          }
+#pragma unroll
+          for (int g = 0; g < G16; ++g) {
+            const int cc = (q0 + qq) * G16 + g;
+            if (cc >= tq.m) break;
+            W xv[RB];
+            ld_xrow<W, RB>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
+#pragma unroll
+            for (int j = 0; j < RB; ++j) acc[j] = fma(d[g], xv[j], acc[j]);
+          }
         }
       }
       const uint8_t* hdr = b.pool + tq.off;
@@ -178,6 +208,7 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
         auto level = [&](auto tc) {
           constexpr int TIER = decltype(tc)::value;
           constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+#pragma unroll 8
           for (int c = 0; c < ru; ++c) {
             const W uv = ldg_fmt<W, TIER>(ucol + ((int64_t)c * kTileRows + r) * eb);
 #pragma unroll
