@@ -10,9 +10,11 @@
 //      lanes over rows, a warp-reduced partial per unit and column of V_q;
 //   2. Y_q = (sum of q's unit partials, in unit order) x the power-of-two
 //      scales of V_q and U_{q^1};
-//   3. per 32-row tile (lane = row): D X from the tile's interleaved
-//      leaf-block part, plus sum_k U_{a_k}[rows, :] Y_{a_k ^ 1} from the
-//      tile's header and U region (a_k the level-k ancestor of its leaf).
+//   3. per leaf (its X rows staged once in the warp's shared-memory slice)
+//      and per 32-row tile of it (lane = row): D X from the tile's
+//      interleaved leaf-block part, plus sum_k U_{a_k}[rows, :] Y_{a_k ^ 1}
+//      from the tile's header and U region (a_k the level-k ancestor), the
+//      U columns through shared memory in double-buffered pieces.
 //
 // hodlr_batch_create uploads the work list and allocates the scratch once;
 // hodlr_batch_run is one kernel launch that allocates and copies nothing.
@@ -38,13 +40,49 @@ struct BItem {
   const int4* units;      // (node, first leaf, end leaf, first partial row)
   const int32_t* node_u;  // [nnodes + 1]: the node's units
   const int32_t* yoff;    // [nnodes]: first row of Y_q
+  const int32_t* leaf_t0; // [nleaves + 1]: the leaf's first tile
   void* Y;                // rows x R
   void* P;                // partial rows x R
   const void* X;
   void* B;
   int64_t ldx, ldb;
-  int32_t depth, R, nnodes, nunits, ntiles, pad_;
+  int32_t depth, R, nnodes, nunits, ntiles, nleaves;
+  int32_t xvec;           // X rows load as 16-byte vectors (R and ldx multiples of 16 / sizeof, X aligned)
+  int32_t pad_;
 };
+
+constexpr int kXSlice = 8192;       // bytes of shared memory per warp for a leaf's X rows
+constexpr int kUPiece = 3072;       // and for each of two pieces of a tile's U columns
+constexpr int kSlice = kXSlice + 2 * kUPiece;
+
+__device__ __forceinline__ int fmt_bytes(int tier) {
+  return tier == HODLR_FP64 ? 8 : tier == HODLR_FP32 ? 4 : (tier == HODLR_E4M3 || tier == HODLR_E5M2) ? 1 : 2;
+}
+
+// 16-byte asynchronous global -> shared copies (completion per commit group)
+__device__ __forceinline__ void bcp16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void bcp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bcp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One stored value of format P from shared memory, in the working precision
+template <typename W, int P>
+__device__ __forceinline__ W lds_fmt(const uint8_t* p) {
+  if constexpr (P == HODLR_FP64) {
+    return (W)*reinterpret_cast<const double*>(p);
+  } else if constexpr (P == HODLR_FP32) {
+    return (W)*reinterpret_cast<const float*>(p);
+  } else if constexpr (P == HODLR_FP16) {
+    return (W)__half2float(__ushort_as_half(*reinterpret_cast<const unsigned short*>(p)));
+  } else if constexpr (P == HODLR_BF16) {
+    return (W)__uint_as_float(((uint32_t)*reinterpret_cast<const unsigned short*>(p)) << 16);
+  } else {
+    __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)*p, P == HODLR_E4M3 ? __NV_E4M3 : __NV_E5M2);
+    return (W)__half2float(*reinterpret_cast<__half*>(&h));
+  }
+}
 
 template <typename W, int P>
 __device__ __forceinline__ W ldg_fmt(const uint8_t* p) {
@@ -63,30 +101,74 @@ __device__ __forceinline__ W ldg_fmt(const uint8_t* p) {
   }
 }
 
+// R values of an X row (zeros past R); XV: as 16-byte vectors (R a multiple
+// of the vector width, the row 16-byte aligned)
+// A staged X row (RB values, zeros past R) from shared memory, as 16-byte
+// vectors when the row length allows
 template <typename W, int RB>
-__device__ __forceinline__ void ld_xrow(const W* x, int R, W (&xv)[RB]) {
+__device__ __forceinline__ void ld_srow(const W* x, W (&xv)[RB]) {
+  if constexpr (RB * sizeof(W) % 16 == 0) {
 #pragma unroll
-  for (int j = 0; j < RB; ++j) xv[j] = j < R ? __ldg(x + j) : (W)0;
+    for (int j4 = 0; j4 < RB * (int)sizeof(W) / 16; ++j4) {
+      const uint4 t = reinterpret_cast<const uint4*>(x)[j4];
+      if constexpr (sizeof(W) == 4) {
+        xv[4 * j4] = __uint_as_float(t.x);
+        xv[4 * j4 + 1] = __uint_as_float(t.y);
+        xv[4 * j4 + 2] = __uint_as_float(t.z);
+        xv[4 * j4 + 3] = __uint_as_float(t.w);
+      } else {
+        xv[2 * j4] = __hiloint2double((int)t.y, (int)t.x);
+        xv[2 * j4 + 1] = __hiloint2double((int)t.w, (int)t.z);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < RB; ++j) xv[j] = x[j];
+  }
+}
+
+template <typename W, int RB, bool XV>
+__device__ __forceinline__ void ld_xrow(const W* x, int R, W (&xv)[RB]) {
+  if constexpr (XV && sizeof(W) == 4 && RB % 4 == 0) {
+#pragma unroll
+    for (int j4 = 0; j4 < RB / 4; ++j4) {
+      const float4 t = 4 * j4 < R ? __ldg(reinterpret_cast<const float4*>(x) + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[4 * j4] = t.x;
+      xv[4 * j4 + 1] = t.y;
+      xv[4 * j4 + 2] = t.z;
+      xv[4 * j4 + 3] = t.w;
+    }
+  } else if constexpr (XV && sizeof(W) == 8 && RB % 2 == 0) {
+#pragma unroll
+    for (int j2 = 0; j2 < RB / 2; ++j2) {
+      const double2 t = 2 * j2 < R ? __ldg(reinterpret_cast<const double2*>(x) + j2) : make_double2(0.0, 0.0);
+      xv[2 * j2] = (W)t.x;
+      xv[2 * j2 + 1] = (W)t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < RB; ++j) xv[j] = j < R ? __ldg(x + j) : (W)0;
+  }
 }
 
 // Row steps unrolled in the V^T X units, V columns per pass and leaf-block
 // chunks loaded ahead in the tile pass: more as the rows get narrower (the
 // registers they take grow with RB).
-template <int RB>
-__host__ __device__ constexpr int batch_unroll() { return RB >= 8 ? 1 : 2; }
-template <int RB>
-__host__ __device__ constexpr int batch_cols() { return RB <= 2 ? 8 : RB <= 4 ? 4 : RB <= 8 ? 2 : 1; }
+template <typename W, int RB>
+__host__ __device__ constexpr int batch_unroll() { return RB <= 2 ? 4 : RB <= 4 ? 2 : 1; }
+template <typename W, int RB>
+__host__ __device__ constexpr int batch_cols() {
+  return sizeof(W) == 4 ? (RB <= 8 ? 8 : 4) : (RB <= 2 ? 8 : RB <= 4 ? 4 : RB <= 8 ? 2 : 1);
+}
 template <int RB>
 __host__ __device__ constexpr int batch_dq() { return RB <= 4 ? 8 : 4; }
 
-template <typename W, int RB>
-__global__ void __launch_bounds__(512, 1)
-batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_first, const int32_t* __restrict__ cta_items) {
+// One matrix's product by the whole CTA (the three steps above).
+template <typename W, int RB, bool XV>
+__device__ void batch_item(const BItem& b) {
   constexpr int es = sizeof(W);
   constexpr int G16 = 16 / es;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int e = cta_first[blockIdx.x]; e < cta_first[blockIdx.x + 1]; ++e) {
-    const BItem& b = items[cta_items[e]];
     const W* X = reinterpret_cast<const W*>(b.X);
     W* Y = reinterpret_cast<W*>(b.Y);
     W* P = reinterpret_cast<W*>(b.P);
@@ -99,7 +181,7 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
       auto unit = [&](auto tc) {
         constexpr int TIER = decltype(tc)::value;
         constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
-        constexpr int CG = batch_cols<RB>();
+        constexpr int CG = batch_cols<W, RB>();
         for (int c0 = 0; c0 < nd.rV; c0 += CG) {
           W acc[CG][RB];
 #pragma unroll
@@ -111,11 +193,11 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
             const int lm = lf.m, lrow0 = lf.row0;
             const uint8_t* col0 = b.pool + nd.offV + ((int64_t)c0 * nd.pm + (lf.prow0 - nd.prow0)) * eb;
             const int64_t cstride = (int64_t)nd.pm * eb;
-            constexpr int kU = batch_unroll<RB>();
+            constexpr int kU = batch_unroll<W, RB>();
 #pragma unroll kU
             for (int r = lane; r < lm; r += 32) {
               W xv[RB];
-              ld_xrow<W, RB>(X + (int64_t)(lrow0 + r) * b.ldx, R, xv);
+              ld_xrow<W, RB, XV>(X + (int64_t)(lrow0 + r) * b.ldx, R, xv);
 #pragma unroll
               for (int a = 0; a < CG; ++a) {
                 // columns past the rank read the last column (never stored)
@@ -154,11 +236,57 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
       }
     }
     __syncthreads();
-    // ---- 3. B rows = D X + U Y, warp per tile, lane = row ----
+    // ---- 3. B rows = D X + U Y.  Warp w takes leaves w, w + nw, ...: the
+    //      leaf's X rows go once into the warp's shared-memory slice (when
+    //      they fit), then its tiles, lane = row ----
     W* B = reinterpret_cast<W*>(b.B);
-    for (int t = warp; t < b.ntiles; t += nw) {
+    extern __shared__ __align__(16) uint8_t bsm[];
+    W* const xs = reinterpret_cast<W*>(bsm + (size_t)warp * kSlice);
+    const uint32_t us = (uint32_t)__cvta_generic_to_shared(bsm + (size_t)warp * kSlice + kXSlice);
+    for (int lf = warp; lf < b.nleaves; lf += nw) {
+    const int lt0 = b.leaf_t0[lf], lt1 = b.leaf_t0[lf + 1];
+    const int lm = b.tiles[lt0].m, lx0 = b.tiles[lt0].xrow0;
+    const bool staged = (int64_t)lm * RB * es <= kXSlice;
+    if (staged) {
+      for (int e2 = lane; e2 < lm * RB; e2 += 32) {
+        const int cc = e2 / RB, j = e2 - cc * RB;
+        xs[e2] = j < R ? __ldg(X + (int64_t)(lx0 + cc) * b.ldx + j) : (W)0;
+      }
+    }
+    __syncwarp();
+    for (int t = lt0; t < lt1; ++t) {
       const P2Tile& tq = b.tiles[t];
       const int r = lane;
+      const uint8_t* hdr = b.pool + tq.off;
+      // The tile's U columns go through shared memory in pieces (whole
+      // columns of one level, at most kUPiece bytes, 16-byte asynchronous
+      // copies): the first piece is requested before the leaf-block part,
+      // each next one before the current one is used.
+      int pk = 1, pc = 0;   // the next piece starts at column pc of level pk
+      auto issue = [&](int buf, int& ko, int& co, int& no) {
+        ko = 0;
+        while (pk <= b.depth) {
+          const uint2 hw = __ldg(reinterpret_cast<const uint2*>(hdr) + (pk - 1));
+          const int ru = (int)(hw.y & 0xffffu);
+          if (pc < ru) {
+            const int eb = fmt_bytes((int)(hw.y >> 16));
+            const int nc = min(ru - pc, kUPiece / (kTileRows * eb));
+            const uint8_t* src = hdr + tq.hbytes + hw.x + (int64_t)pc * kTileRows * eb;
+            const int nv = nc * kTileRows * eb / 16;
+            for (int v = lane; v < nv; v += 32) bcp16(us + buf * kUPiece + v * 16, src + v * 16);
+            ko = pk;
+            co = pc;
+            no = nc;
+            pc += nc;
+            break;
+          }
+          ++pk;
+          pc = 0;
+        }
+        bcp_commit();
+      };
+      int ck, cc0, cn;
+      issue(0, ck, cc0, cn);
       W acc[RB];
 #pragma unroll
       for (int j = 0; j < RB; ++j) acc[j] = (W)0;
@@ -166,14 +294,20 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
       const int nchunk = (tq.m + G16 - 1) / G16;
       // DQ chunks of the leaf-block row loaded before any is used (16-byte
       // vectors, consecutive lanes consecutive rows); the X rows are the same
-      // on every lane (one broadcast transaction each)
+      // on every lane (shared-memory broadcasts when staged)
       constexpr int DQ = batch_dq<RB>();
+      // two groups in flight: group q0 + DQ is requested before group q0 is used
+      uint4 raw[DQ], nxt[DQ];
+#pragma unroll
+      for (int qq = 0; qq < DQ; ++qq)
+        raw[qq] = qq < nchunk ? __ldg(reinterpret_cast<const uint4*>(d2 + (int64_t)qq * kTileRows * 16))
+                              : make_uint4(0u, 0u, 0u, 0u);
       for (int q0 = 0; q0 < nchunk; q0 += DQ) {
-        uint4 raw[DQ];
 #pragma unroll
         for (int qq = 0; qq < DQ; ++qq)
-          raw[qq] = q0 + qq < nchunk ? __ldg(reinterpret_cast<const uint4*>(d2 + (int64_t)(q0 + qq) * kTileRows * 16))
-                                     : make_uint4(0u, 0u, 0u, 0u);
+          nxt[qq] = q0 + DQ + qq < nchunk
+                        ? __ldg(reinterpret_cast<const uint4*>(d2 + (int64_t)(q0 + DQ + qq) * kTileRows * 16))
+                        : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
         for (int qq = 0; qq < DQ; ++qq) {
           W d[G16];
@@ -191,32 +325,44 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
             const int cc = (q0 + qq) * G16 + g;
             if (cc >= tq.m) break;
             W xv[RB];
-            ld_xrow<W, RB>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
+            if (staged)
+              ld_srow<W, RB>(xs + cc * RB, xv);
+            else
+              ld_xrow<W, RB, XV>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
 #pragma unroll
             for (int j = 0; j < RB; ++j) acc[j] = fma(d[g], xv[j], acc[j]);
           }
         }
+#pragma unroll
+        for (int qq = 0; qq < DQ; ++qq) raw[qq] = nxt[qq];
       }
-      const uint8_t* hdr = b.pool + tq.off;
-      for (int k = 1; k <= b.depth; ++k) {
-        const uint2 hw = *reinterpret_cast<const uint2*>(hdr + 8 * (k - 1));
-        const int ru = (int)(hw.y & 0xffffu), tier = (int)(hw.y >> 16);
-        if (ru == 0) continue;
-        const int sib = node_index(k, (tq.leaf >> (b.depth - k)) ^ 1);
-        const W* yb = Y + (int64_t)b.yoff[sib] * R;
-        const uint8_t* ucol = hdr + tq.hbytes + hw.x;
+      int buf = 0;
+      while (ck) {
+        int nk, nc0, nn;
+        issue(buf ^ 1, nk, nc0, nn);
+        if (nk) bcp_wait<1>(); else bcp_wait<0>();
+        __syncwarp();   // every lane's copies of the current piece have landed
+        const int tier = (int)(__ldg(reinterpret_cast<const uint2*>(hdr) + (ck - 1)).y >> 16);
+        const int sib = node_index(ck, (tq.leaf >> (b.depth - ck)) ^ 1);
+        const W* yb = Y + ((int64_t)b.yoff[sib] + cc0) * R;
+        const uint8_t* up = bsm + (size_t)warp * kSlice + kXSlice + buf * kUPiece;
         auto level = [&](auto tc) {
           constexpr int TIER = decltype(tc)::value;
           constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
 #pragma unroll 8
-          for (int c = 0; c < ru; ++c) {
-            const W uv = ldg_fmt<W, TIER>(ucol + ((int64_t)c * kTileRows + r) * eb);
+          for (int c = 0; c < cn; ++c) {
+            const W uv = lds_fmt<W, TIER>(up + (c * kTileRows + r) * eb);
 #pragma unroll
             for (int j = 0; j < RB; ++j)
               if (j < R) acc[j] = fma(uv, yb[c * R + j], acc[j]);
           }
         };
         with_format(tier, level);
+        __syncwarp();   // the piece is read before its buffer is refilled
+        ck = nk;
+        cc0 = nc0;
+        cn = nn;
+        buf ^= 1;
       }
       if (r < tq.rows) {
         W* brow = B + (int64_t)(tq.row0 + r) * b.ldb;
@@ -225,21 +371,47 @@ batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_fi
           if (j < R) brow[j] = acc[j];
       }
     }
+    __syncwarp();   // the slice is read before the next leaf's rows overwrite it
+    }
+}
+
+template <typename W, int RB>
+__global__ void __launch_bounds__(512, 1)
+batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_first, const int32_t* __restrict__ cta_items) {
+  for (int e = cta_first[blockIdx.x]; e < cta_first[blockIdx.x + 1]; ++e) {
+    const BItem& b = items[cta_items[e]];
+    if (b.xvec)
+      batch_item<W, RB, true>(b);
+    else
+      batch_item<W, RB, false>(b);
     __syncthreads();
   }
+}
+
+template <typename W, int RB>
+cudaError_t launch_batch_rb(int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
+                            cudaStream_t s) {
+  const int smem = (threads / 32) * kSlice;
+  static int smem_set = 0;   // per instantiation: largest size opted in so far
+  if (smem > smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<W, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    smem_set = smem;
+  }
+  batch_kernel<W, RB><<<grid, threads, smem, s>>>(items, first, list);
+  return cudaGetLastError();
 }
 
 template <typename W>
 cudaError_t launch_batch_w(int rb, int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
                            cudaStream_t s) {
   switch (rb) {
-    case 1: batch_kernel<W, 1><<<grid, threads, 0, s>>>(items, first, list); break;
-    case 2: batch_kernel<W, 2><<<grid, threads, 0, s>>>(items, first, list); break;
-    case 4: batch_kernel<W, 4><<<grid, threads, 0, s>>>(items, first, list); break;
-    case 8: batch_kernel<W, 8><<<grid, threads, 0, s>>>(items, first, list); break;
-    default: batch_kernel<W, 16><<<grid, threads, 0, s>>>(items, first, list); break;
+    case 1: return launch_batch_rb<W, 1>(grid, threads, items, first, list, s);
+    case 2: return launch_batch_rb<W, 2>(grid, threads, items, first, list, s);
+    case 4: return launch_batch_rb<W, 4>(grid, threads, items, first, list, s);
+    case 8: return launch_batch_rb<W, 8>(grid, threads, items, first, list, s);
+    default: return launch_batch_rb<W, 16>(grid, threads, items, first, list, s);
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -291,7 +463,7 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
   bt->rb = rmax <= 1 ? 1 : rmax <= 2 ? 2 : rmax <= 4 ? 4 : rmax <= 8 ? 8 : 16;
   // work lists: units, node_u, yoff (int32 words) of every item, scratch rows
   std::vector<int32_t> meta;
-  std::vector<size_t> meta_units(count), meta_nodeu(count), meta_yoff(count);
+  std::vector<size_t> meta_units(count), meta_nodeu(count), meta_yoff(count), meta_lt0(count);
   std::vector<int64_t> y_off(count), p_off(count);
   std::vector<BItem> items(count);
   std::vector<int> nunits(count);
@@ -333,6 +505,13 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
     meta.insert(meta.end(), node_u.begin(), node_u.end());
     meta_yoff[i] = meta.size();
     meta.insert(meta.end(), yoff.begin(), yoff.end());
+    {
+      const int nleaves = (int)h->leaves.size();
+      std::vector<int32_t> lt0(nleaves + 1, (int)h->p2.size());
+      for (int t = (int)h->p2.size() - 1; t >= 0; --t) lt0[h->p2[t].leaf] = t;
+      meta_lt0[i] = meta.size();
+      meta.insert(meta.end(), lt0.begin(), lt0.end());
+    }
     y_off[i] = scratch;
     scratch += (int64_t)std::max(yrows, 1) * nrhs[i];
     p_off[i] = scratch;
@@ -352,6 +531,11 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
     it.nnodes = nnodes;
     it.nunits = nunits[i];
     it.ntiles = (int)h->p2.size();
+    it.nleaves = (int)h->leaves.size();
+    {
+      const int vw = 16 / es;   // elements per 16-byte vector
+      it.xvec = nrhs[i] % vw == 0 && ldx[i] % vw == 0 && reinterpret_cast<uintptr_t>(X[i]) % 16 == 0 ? 1 : 0;
+    }
     cost[i] = (double)(h->info.leaf_bytes + h->info.factor_bytes) + 2.0 * h->n * nrhs[i] * es;
   }
   e = cudaMalloc(&bt->d_meta, std::max<size_t>(meta.size(), 4) * sizeof(int32_t));
@@ -370,6 +554,7 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
     items[i].units = reinterpret_cast<const int4*>(dm + meta_units[i]);
     items[i].node_u = dm + meta_nodeu[i];
     items[i].yoff = dm + meta_yoff[i];
+    items[i].leaf_t0 = dm + meta_lt0[i];
     items[i].Y = (uint8_t*)bt->d_scratch + (size_t)y_off[i] * es;
     items[i].P = (uint8_t*)bt->d_scratch + (size_t)p_off[i] * es;
   }
