@@ -48,7 +48,7 @@ struct BItem {
   int64_t ldx, ldb;
   int32_t depth, R, nnodes, nunits, ntiles, nleaves;
   int32_t xvec;           // X rows load as 16-byte vectors (R and ldx multiples of 16 / sizeof, X aligned)
-  int32_t pad_;
+  int32_t rb;             // R rounded up to 1, 2, 4, 8 or 16: the item's column block and Y's row stride
 };
 
 constexpr int kXSlice = 8192;       // bytes of shared memory per warp for a leaf's X rows
@@ -103,10 +103,11 @@ __device__ __forceinline__ W ldg_fmt(const uint8_t* p) {
 
 // R values of an X row (zeros past R); XV: as 16-byte vectors (R a multiple
 // of the vector width, the row 16-byte aligned)
-// A staged X row (RB values, zeros past R) from shared memory, as 16-byte
-// vectors when the row length allows
+// A row of RB values (a staged X row in shared memory, zeros past R, or a
+// row of Y written earlier in this launch: plain loads), as 16-byte vectors
+// when the row length allows
 template <typename W, int RB>
-__device__ __forceinline__ void ld_srow(const W* x, W (&xv)[RB]) {
+__device__ __forceinline__ void ld_row(const W* x, W (&xv)[RB]) {
   if constexpr (RB * sizeof(W) % 16 == 0) {
 #pragma unroll
     for (int j4 = 0; j4 < RB * (int)sizeof(W) / 16; ++j4) {
@@ -164,8 +165,10 @@ template <int RB>
 __host__ __device__ constexpr int batch_dq() { return RB <= 4 ? 8 : 4; }
 
 // One matrix's product by the whole CTA (the three steps above).
+// Not inlined: each column block gets its own register allocation (inlined
+// into one kernel, the widest block's spills reached every item).
 template <typename W, int RB, bool XV>
-__device__ void batch_item(const BItem& b) {
+__device__ __noinline__ void batch_item(const BItem& b) {
   constexpr int es = sizeof(W);
   constexpr int G16 = 16 / es;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -228,11 +231,12 @@ __device__ void batch_item(const BItem& b) {
       const NodeDev& nd = b.nodes[q];
       const W sc = (W)(nd.invsV * b.nodes[q ^ 1].invsU);
       const int u0 = b.node_u[q], u1 = b.node_u[q + 1];
-      for (int e2 = lane; e2 < nd.rV * R; e2 += 32) {
-        const int c = e2 / R, j = e2 - c * R;
+      for (int e2 = lane; e2 < nd.rV * RB; e2 += 32) {
+        const int c = e2 / RB, j = e2 - c * RB;
         W s = (W)0;
-        for (int u = u0; u < u1; ++u) s += P[(int64_t)(b.units[u].w + c) * R + j];
-        Y[(int64_t)(b.yoff[q] + c) * R + j] = s * sc;
+        if (j < R)
+          for (int u = u0; u < u1; ++u) s += P[(int64_t)(b.units[u].w + c) * R + j];
+        Y[(int64_t)(b.yoff[q] + c) * RB + j] = s * sc;   // rows of RB values, zeros past R
       }
     }
     __syncthreads();
@@ -326,7 +330,7 @@ __device__ void batch_item(const BItem& b) {
             if (cc >= tq.m) break;
             W xv[RB];
             if (staged)
-              ld_srow<W, RB>(xs + cc * RB, xv);
+              ld_row<W, RB>(xs + cc * RB, xv);
             else
               ld_xrow<W, RB, XV>(X + (int64_t)(tq.xrow0 + cc) * b.ldx, R, xv);
 #pragma unroll
@@ -344,7 +348,7 @@ __device__ void batch_item(const BItem& b) {
         __syncwarp();   // every lane's copies of the current piece have landed
         const int tier = (int)(__ldg(reinterpret_cast<const uint2*>(hdr) + (ck - 1)).y >> 16);
         const int sib = node_index(ck, (tq.leaf >> (b.depth - ck)) ^ 1);
-        const W* yb = Y + ((int64_t)b.yoff[sib] + cc0) * R;
+        const W* yb = Y + ((int64_t)b.yoff[sib] + cc0) * RB;
         const uint8_t* up = bsm + (size_t)warp * kSlice + kXSlice + buf * kUPiece;
         auto level = [&](auto tc) {
           constexpr int TIER = decltype(tc)::value;
@@ -352,9 +356,10 @@ __device__ void batch_item(const BItem& b) {
 #pragma unroll 8
           for (int c = 0; c < cn; ++c) {
             const W uv = lds_fmt<W, TIER>(up + (c * kTileRows + r) * eb);
+            W yv[RB];
+            ld_row<W, RB>(yb + c * RB, yv);
 #pragma unroll
-            for (int j = 0; j < RB; ++j)
-              if (j < R) acc[j] = fma(uv, yb[c * R + j], acc[j]);
+            for (int j = 0; j < RB; ++j) acc[j] = fma(uv, yv[j], acc[j]);
           }
         };
         with_format(tier, level);
@@ -376,42 +381,43 @@ __device__ void batch_item(const BItem& b) {
 }
 
 template <typename W, int RB>
+__device__ __forceinline__ void batch_item_rb(const BItem& b) {
+  if (b.xvec)
+    batch_item<W, RB, true>(b);
+  else
+    batch_item<W, RB, false>(b);
+}
+
+// Each item runs with its own column block (so one with few right-hand
+// sides does no work for the widest item's columns).
+template <typename W>
 __global__ void __launch_bounds__(512, 1)
 batch_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ cta_first, const int32_t* __restrict__ cta_items) {
   for (int e = cta_first[blockIdx.x]; e < cta_first[blockIdx.x + 1]; ++e) {
     const BItem& b = items[cta_items[e]];
-    if (b.xvec)
-      batch_item<W, RB, true>(b);
-    else
-      batch_item<W, RB, false>(b);
+    switch (b.rb) {
+      case 1: batch_item_rb<W, 1>(b); break;
+      case 2: batch_item_rb<W, 2>(b); break;
+      case 4: batch_item_rb<W, 4>(b); break;
+      case 8: batch_item_rb<W, 8>(b); break;
+      default: batch_item_rb<W, 16>(b); break;
+    }
     __syncthreads();
   }
 }
 
-template <typename W, int RB>
-cudaError_t launch_batch_rb(int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
-                            cudaStream_t s) {
+template <typename W>
+cudaError_t launch_batch_w(int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
+                           cudaStream_t s) {
   const int smem = (threads / 32) * kSlice;
   static int smem_set = 0;   // per instantiation: largest size opted in so far
   if (smem > smem_set) {
-    cudaError_t e = cudaFuncSetAttribute(batch_kernel<W, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
-  batch_kernel<W, RB><<<grid, threads, smem, s>>>(items, first, list);
+  batch_kernel<W><<<grid, threads, smem, s>>>(items, first, list);
   return cudaGetLastError();
-}
-
-template <typename W>
-cudaError_t launch_batch_w(int rb, int grid, int threads, const BItem* items, const int32_t* first, const int32_t* list,
-                           cudaStream_t s) {
-  switch (rb) {
-    case 1: return launch_batch_rb<W, 1>(grid, threads, items, first, list, s);
-    case 2: return launch_batch_rb<W, 2>(grid, threads, items, first, list, s);
-    case 4: return launch_batch_rb<W, 4>(grid, threads, items, first, list, s);
-    case 8: return launch_batch_rb<W, 8>(grid, threads, items, first, list, s);
-    default: return launch_batch_rb<W, 16>(grid, threads, items, first, list, s);
-  }
 }
 
 }  // namespace
@@ -420,7 +426,7 @@ cudaError_t launch_batch_w(int rb, int grid, int threads, const BItem* items, co
 using namespace hodlr;
 
 struct hodlr_batch_s {
-  int count = 0, work = HODLR_FP32, rb = 1, grid = 1, threads = 256, device = 0;
+  int count = 0, work = HODLR_FP32, grid = 1, threads = 256, device = 0;
   BItem* d_items = nullptr;
   int32_t* d_first = nullptr;
   int32_t* d_list = nullptr;
@@ -446,7 +452,6 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
   if (e != cudaSuccess) return set_cuda_error(e, "cudaGetDevice");
   if (xb_prec != HODLR_FP32 && xb_prec != HODLR_FP64) return set_error(HODLR_EINVAL, "X/B precision must be fp32 or fp64");
   const int es = prec_bytes(xb_prec);
-  int rmax = 1;
   for (int i = 0; i < count; ++i) {
     const hodlr_t h = hs[i];
     if (!h) return set_error(HODLR_EINVAL, "null handle in the batch");
@@ -454,13 +459,11 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
     if (h->work != xb_prec) return set_error(HODLR_EINVAL, "X/B type must equal every matrix's working precision");
     if (nrhs[i] < 1 || nrhs[i] > kBatchMaxCols) return set_error(HODLR_EINVAL, "nrhs must be in [1, 16]");
     if (!X[i] || !B[i] || ldx[i] < nrhs[i] || ldb[i] < nrhs[i]) return set_error(HODLR_EINVAL, "bad X/B of an item");
-    rmax = std::max(rmax, (int)nrhs[i]);
   }
   hodlr_batch_s* bt = new hodlr_batch_s();
   bt->count = count;
   bt->work = xb_prec;
   bt->device = dev;
-  bt->rb = rmax <= 1 ? 1 : rmax <= 2 ? 2 : rmax <= 4 ? 4 : rmax <= 8 ? 8 : 16;
   // work lists: units, node_u, yoff (int32 words) of every item, scratch rows
   std::vector<int32_t> meta;
   std::vector<size_t> meta_units(count), meta_nodeu(count), meta_yoff(count), meta_lt0(count);
@@ -512,8 +515,10 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
       meta_lt0[i] = meta.size();
       meta.insert(meta.end(), lt0.begin(), lt0.end());
     }
+    const int rb = nrhs[i] <= 1 ? 1 : nrhs[i] <= 2 ? 2 : nrhs[i] <= 4 ? 4 : nrhs[i] <= 8 ? 8 : 16;
+    scratch = (scratch + 16 / es - 1) / (16 / es) * (16 / es);   // Y rows load as 16-byte vectors
     y_off[i] = scratch;
-    scratch += (int64_t)std::max(yrows, 1) * nrhs[i];
+    scratch += (int64_t)std::max(yrows, 1) * rb;
     p_off[i] = scratch;
     scratch += (int64_t)std::max(poff, 1) * nrhs[i];
     BItem& it = items[i];
@@ -532,10 +537,13 @@ extern "C" hodlr_status hodlr_batch_create(int32_t count, const hodlr_t* hs, con
     it.nunits = nunits[i];
     it.ntiles = (int)h->p2.size();
     it.nleaves = (int)h->leaves.size();
+    it.rb = rb;
     {
       const int vw = 16 / es;   // elements per 16-byte vector
       it.xvec = nrhs[i] % vw == 0 && ldx[i] % vw == 0 && reinterpret_cast<uintptr_t>(X[i]) % 16 == 0 ? 1 : 0;
     }
+    // bytes read and written (measured: dealing by a multiply-add count
+    // instead balanced the CTAs worse)
     cost[i] = (double)(h->info.leaf_bytes + h->info.factor_bytes) + 2.0 * h->n * nrhs[i] * es;
   }
   e = cudaMalloc(&bt->d_meta, std::max<size_t>(meta.size(), 4) * sizeof(int32_t));
@@ -598,8 +606,8 @@ extern "C" hodlr_status hodlr_batch_run(hodlr_batch_t b, int32_t threads, void* 
   if (threads != 128 && threads != 256 && threads != 512) return set_error(HODLR_EINVAL, "threads must be 128, 256 or 512");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = b->work == HODLR_FP64
-                      ? launch_batch_w<double>(b->rb, b->grid, threads, b->d_items, b->d_first, b->d_list, s)
-                      : launch_batch_w<float>(b->rb, b->grid, threads, b->d_items, b->d_first, b->d_list, s);
+                      ? launch_batch_w<double>(b->grid, threads, b->d_items, b->d_first, b->d_list, s)
+                      : launch_batch_w<float>(b->grid, threads, b->d_items, b->d_first, b->d_list, s);
   return e == cudaSuccess ? HODLR_OK : set_cuda_error(e, "hodlr_batch_run");
 }
 
