@@ -391,6 +391,55 @@ hodlr_status hodlr_batch_tune(hodlr_batch_t b, void* stream, int32_t* best_threa
  * is a no-op. */
 void hodlr_batch_destroy(hodlr_batch_t b);
 
+/* ---- Partitioned product (Algorithm 3.3 split by rows) ------------------ */
+
+/* A row-partitioned product B = H X over P = 2^g parts (one per GPU, or one
+ * per stream): part j owns the rows of node (g, j) of the cluster tree
+ * (Def. 2.1), i.e. its 2^(depth-g) leaves.  In Algorithm 3.3 the products
+ * V^T x of the levels k > g inside (g, j) need only the part's rows; those of
+ * levels k <= g sum over the parts.  So each part computes, from its own X
+ * rows only:
+ *   1. hodlr_part_partial: V_q^T X over its rows for every node q, the
+ *      levels 1..g into the caller's buffer Yred (zeros for the nodes that
+ *      are not its ancestors), the rest into the part's scratch;
+ *   2. the caller sums Yred over the P parts (an all-reduce: sum) -- the
+ *      only exchange, yred_count values (sum over levels k <= g of the
+ *      ranks, times R rounded up to 1, 2, 4, 8 or 16);
+ *   3. hodlr_part_finish: its B rows = D X + sum_k U_k Y_k, the levels <= g
+ *      from the summed Yred.
+ * No X or factor bytes cross parts.  The handle is shared (each part reads
+ * only its rows' data).  g = 0 is one part: the whole product. */
+typedef struct hodlr_part_s* hodlr_part_t;
+
+/* hodlr_part_create -- plan part j (0 <= j < 2^g, 0 <= g <= depth) of h for
+ * nrhs in [1, 16] right-hand sides: uploads its work list, allocates its
+ * scratch.  The handle must outlive the part.  Synchronous.
+ * Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_part_create(hodlr_t h, int32_t g, int32_t j, int32_t nrhs, hodlr_part_t* out);
+
+/* hodlr_part_info -- the part's first row and rows (X and B of the part hold
+ * rows row0 .. row0 + rows - 1 of the whole product) and the length of Yred
+ * in elements of the working precision (0 when g = 0).  Outputs may be NULL. */
+hodlr_status hodlr_part_info(hodlr_part_t p, int64_t* row0, int64_t* rows, int64_t* yred_count);
+
+/* hodlr_part_partial -- step 1 on `stream`.  X: device (rows, nrhs) of the
+ * working precision, row-major, ldx >= nrhs (the part's rows only).  Yred:
+ * device, yred_count elements, overwritten (may be NULL when yred_count is
+ * 0).  Allocates nothing.  Steps 1 and 3 of one part use its scratch: run
+ * them in order, one product at a time.  Errors: HODLR_EINVAL, HODLR_ECUDA. */
+hodlr_status hodlr_part_partial(hodlr_part_t p, const void* X, int64_t ldx, void* Yred, void* stream);
+
+/* hodlr_part_finish -- step 3 on `stream`: B (device (rows, nrhs), ldb >=
+ * nrhs) = the part's rows of H X, from the same X and from Yred holding the
+ * sum over all parts.  Allocates nothing.  Errors: HODLR_EINVAL,
+ * HODLR_ECUDA. */
+hodlr_status hodlr_part_finish(hodlr_part_t p, const void* X, int64_t ldx, const void* Yred, void* B, int64_t ldb,
+                               void* stream);
+
+/* hodlr_part_destroy -- free the part (its scratch; cudaFree waits for its
+ * device work).  NULL is a no-op. */
+void hodlr_part_destroy(hodlr_part_t p);
+
 /* hodlr_node_sizes -- per node (layout as ranks in hodlr_import: node
  * q = 2^k - 2 + i is (k, i), k = 1..depth) its first row and its rows, the
  * ceil-half cluster tree of Def. 2.1 (the leaves are the level-depth nodes;

@@ -95,6 +95,12 @@ SIGNATURES = {
     "hodlr_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "hodlr_batch_tune": (ctypes.c_int, [_P, _P, _I32P, ctypes.POINTER(ctypes.c_float)]),
     "hodlr_batch_destroy": (None, [_P]),
+    "hodlr_part_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "hodlr_part_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "hodlr_part_partial": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "hodlr_part_finish": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, ctypes.c_int64, _P]),
+    "hodlr_part_destroy": (None, [_P]),
     "hodlr_mlp_num_params": (ctypes.c_int32, []),
     "hodlr_mlp_features": (ctypes.c_int, [ctypes.POINTER(Kernel), _P, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_double, _P, _P]),

@@ -10,10 +10,12 @@
 //  features  per block (k, i): k / 12, log2(m) / 20, log10(eps) / 10 and the
 //            log10 of eight row norms of the block (rows (2j + 1) m / 16,
 //            all of its columns) over the largest of them, / 10;
-//  forward   one thread per sample, the weights broadcast from shared memory;
+//  forward   one warp per sample (two hidden units per lane, inputs broadcast
+//            by shuffles), the weights in shared memory;
 //  backward  per-sample deltas, then one thread per parameter summing over
 //            the samples in order (no atomics: reproducible);
 //  adam      one thread per parameter on fp32 master weights, fp16 copy.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -62,80 +64,105 @@ __global__ void __launch_bounds__(256) features_kernel(const double* __restrict_
   }
 }
 
-// one sample per thread: y and the pre-activations z1, z2, z3
-__global__ void __launch_bounds__(128) forward_kernel(const __half* __restrict__ w16, int S, const float* __restrict__ X,
-                                                      float* __restrict__ y, float* __restrict__ act) {
-  __shared__ float w[kP];
-  for (int e = threadIdx.x; e < kP; e += blockDim.x) w[e] = __half2float(w16[e]);
-  __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  float x[kIn], ha[kHid], hb[kHid];
-#pragma unroll
-  for (int j = 0; j < kIn; ++j) x[j] = X[(int64_t)s * kIn + j];
-  float* za = act ? act + (int64_t)s * kAct : nullptr;
-#pragma unroll
-  for (int i = 0; i < kHid; ++i) {
-    float z = w[oB1 + i];
-#pragma unroll
-    for (int j = 0; j < kIn; ++j) z = fmaf(w[oW1 + i * kIn + j], x[j], z);
-    if (za) za[i] = z;
-    ha[i] = fmaxf(z, 0.0f);
-  }
-#pragma unroll
-  for (int i = 0; i < kHid; ++i) {
-    float z = w[oB2 + i];
-#pragma unroll
-    for (int j = 0; j < kHid; ++j) z = fmaf(w[oW2 + i * kHid + j], ha[j], z);
-    if (za) za[kHid + i] = z;
-    hb[i] = fmaxf(z, 0.0f);
-  }
-#pragma unroll
-  for (int i = 0; i < kHid; ++i) {
-    float z = w[oB3 + i];
-#pragma unroll
-    for (int j = 0; j < kHid; ++j) z = fmaf(w[oW3 + i * kHid + j], hb[j], z);
-    if (za) za[2 * kHid + i] = z;
-    ha[i] = fmaxf(z, 0.0f);
-  }
-  float o = w[oB4];
-#pragma unroll
-  for (int j = 0; j < kHid; ++j) o = fmaf(w[oW4 + j], ha[j], o);
-  y[s] = o;
+// One warp per sample: lane l holds hidden units l and l + 32; the inputs of
+// a layer are broadcast from their lanes by shuffles, and every sum runs
+// over its inputs in ascending order from the bias (the order of the
+// layer definitions).  Weight matrices sit transposed in shared memory
+// (input-major), so the lanes of one input read consecutive words.
+constexpr int kMlpThreads = 256;
+
+__device__ __forceinline__ int mlp_wt(int p) {   // parameter index -> shared-memory index
+  if (p < oB1) return oW1 + (p % kIn) * kHid + p / kIn;
+  if (p >= oW2 && p < oB2) return oW2 + ((p - oW2) % kHid) * kHid + (p - oW2) / kHid;
+  if (p >= oW3 && p < oB3) return oW3 + ((p - oW3) % kHid) * kHid + (p - oW3) / kHid;
+  return p;
 }
 
-// per-sample deltas d1, d2, d3 (dL/dz of each hidden layer) from dy
-__global__ void __launch_bounds__(128) delta_kernel(const __half* __restrict__ w16, int S, const float* __restrict__ act,
-                                                    const float* __restrict__ dy, float* __restrict__ del) {
+// y and the pre-activations z1, z2, z3
+__global__ void __launch_bounds__(kMlpThreads) forward_kernel(const __half* __restrict__ w16, int S,
+                                                              const float* __restrict__ X, float* __restrict__ y,
+                                                              float* __restrict__ act) {
+  __shared__ float w[kP];
+  for (int e = threadIdx.x; e < kP; e += blockDim.x) w[mlp_wt(e)] = __half2float(w16[e]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int s = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nwarp) {
+    const float x = lane < kIn ? X[(int64_t)s * kIn + lane] : 0.0f;
+    float* za = act ? act + (int64_t)s * kAct : nullptr;
+    float z0 = w[oB1 + lane], z1 = w[oB1 + 32 + lane];
+#pragma unroll
+    for (int j = 0; j < kIn; ++j) {
+      const float xj = __shfl_sync(0xffffffffu, x, j);
+      z0 = fmaf(w[oW1 + j * kHid + lane], xj, z0);
+      z1 = fmaf(w[oW1 + j * kHid + 32 + lane], xj, z1);
+    }
+    if (za) { za[lane] = z0; za[32 + lane] = z1; }
+    float h0 = fmaxf(z0, 0.0f), h1 = fmaxf(z1, 0.0f);
+#pragma unroll
+    for (int layer = 0; layer < 2; ++layer) {
+      const int oW = layer ? oW3 : oW2, oB = layer ? oB3 : oB2;
+      z0 = w[oB + lane];
+      z1 = w[oB + 32 + lane];
+#pragma unroll
+      for (int j = 0; j < kHid; ++j) {
+        const float hj = __shfl_sync(0xffffffffu, j < 32 ? h0 : h1, j & 31);
+        z0 = fmaf(w[oW + j * kHid + lane], hj, z0);
+        z1 = fmaf(w[oW + j * kHid + 32 + lane], hj, z1);
+      }
+      if (za) { za[(layer + 1) * kHid + lane] = z0; za[(layer + 1) * kHid + 32 + lane] = z1; }
+      h0 = fmaxf(z0, 0.0f);
+      h1 = fmaxf(z1, 0.0f);
+    }
+    float o = w[oB4];   // every lane forms the same sum, in order
+#pragma unroll
+    for (int j = 0; j < kHid; ++j) o = fmaf(w[oW4 + j], __shfl_sync(0xffffffffu, j < 32 ? h0 : h1, j & 31), o);
+    if (lane == 0) y[s] = o;
+  }
+}
+
+// per-sample deltas d1, d2, d3 (dL/dz of each hidden layer) from dy; the
+// weights in their own (output-major) layout: the lanes of one output row
+// read consecutive words
+__global__ void __launch_bounds__(kMlpThreads) delta_kernel(const __half* __restrict__ w16, int S,
+                                                            const float* __restrict__ act, const float* __restrict__ dy,
+                                                            float* __restrict__ del) {
   __shared__ float w[kP];
   for (int e = threadIdx.x; e < kP; e += blockDim.x) w[e] = __half2float(w16[e]);
   __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= S) return;
-  const float* z = act + (int64_t)s * kAct;
-  float* d = del + (int64_t)s * kAct;
-  float da[kHid], db[kHid];
-  const float g = dy[s];
+  const int lane = threadIdx.x & 31;
+  const int nwarp = (int)(gridDim.x * blockDim.x) >> 5;
+  for (int s = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nwarp) {
+    const float* z = act + (int64_t)s * kAct;
+    float* d = del + (int64_t)s * kAct;
+    const float g = dy[s];
+    float d0 = z[2 * kHid + lane] > 0.0f ? g * w[oW4 + lane] : 0.0f;   // d3
+    float d1 = z[2 * kHid + 32 + lane] > 0.0f ? g * w[oW4 + 32 + lane] : 0.0f;
+    d[2 * kHid + lane] = d0;
+    d[2 * kHid + 32 + lane] = d1;
 #pragma unroll
-  for (int i = 0; i < kHid; ++i) {
-    da[i] = z[2 * kHid + i] > 0.0f ? g * w[oW4 + i] : 0.0f;   // d3
-    d[2 * kHid + i] = da[i];
+    for (int layer = 1; layer >= 0; --layer) {   // d2 = (W3^T d3) * relu'(z2), d1 = (W2^T d2) * relu'(z1)
+      const int oW = layer ? oW3 : oW2;
+      float t0 = 0.0f, t1 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < kHid; ++i) {
+        const float di = __shfl_sync(0xffffffffu, i < 32 ? d0 : d1, i & 31);
+        t0 = fmaf(w[oW + i * kHid + lane], di, t0);
+        t1 = fmaf(w[oW + i * kHid + 32 + lane], di, t1);
+      }
+      d0 = z[layer * kHid + lane] > 0.0f ? t0 : 0.0f;
+      d1 = z[layer * kHid + 32 + lane] > 0.0f ? t1 : 0.0f;
+      d[layer * kHid + lane] = d0;
+      d[layer * kHid + 32 + lane] = d1;
+    }
   }
-#pragma unroll
-  for (int j = 0; j < kHid; ++j) {   // d2 = (W3^T d3) * relu'(z2)
-    float t = 0.0f;
-#pragma unroll
-    for (int i = 0; i < kHid; ++i) t = fmaf(w[oW3 + i * kHid + j], da[i], t);
-    db[j] = z[kHid + j] > 0.0f ? t : 0.0f;
-    d[kHid + j] = db[j];
-  }
-#pragma unroll
-  for (int j = 0; j < kHid; ++j) {   // d1 = (W2^T d2) * relu'(z1)
-    float t = 0.0f;
-#pragma unroll
-    for (int i = 0; i < kHid; ++i) t = fmaf(w[oW2 + i * kHid + j], db[i], t);
-    d[j] = z[j] > 0.0f ? t : 0.0f;
-  }
+}
+
+// CTAs for S samples at one warp each (at most two per SM's worth: each CTA
+// loads all the weights once)
+static unsigned mlp_grid(int S) {
+  const int per = kMlpThreads / 32;
+  return (unsigned)std::max(1, std::min((S + per - 1) / per, 2 * 152));
 }
 
 // one thread per parameter: the sum over samples (in order) of delta x input
@@ -248,7 +275,7 @@ extern "C" hodlr_status hodlr_mlp_forward(const uint16_t* w16, int32_t S, const 
                                           void* stream) {
   if (!w16 || !X || !y || S < 0) return set_error(HODLR_EINVAL, "bad hodlr_mlp_forward arguments");
   if (S == 0) return HODLR_OK;
-  forward_kernel<<<(unsigned)((S + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+  forward_kernel<<<mlp_grid(S), kMlpThreads, 0, (cudaStream_t)stream>>>(
       reinterpret_cast<const __half*>(w16), S, X, y, act);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HODLR_OK : set_cuda_error(e, "hodlr_mlp_forward");
@@ -267,7 +294,7 @@ extern "C" hodlr_status hodlr_mlp_backward(const uint16_t* w16, int32_t S, const
   if (!w16 || !X || !act || !dy || !grad || !work || S < 1)
     return set_error(HODLR_EINVAL, "bad hodlr_mlp_backward arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  delta_kernel<<<(unsigned)((S + 127) / 128), 128, 0, s>>>(reinterpret_cast<const __half*>(w16), S, act, dy, work);
+  delta_kernel<<<mlp_grid(S), kMlpThreads, 0, s>>>(reinterpret_cast<const __half*>(w16), S, act, dy, work);
   grad_kernel<<<(unsigned)((kP + 255) / 256), 256, 0, s>>>(S, X, act, work, dy, grad);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HODLR_OK : set_cuda_error(e, "hodlr_mlp_backward");

@@ -456,6 +456,64 @@ class HodlrBatch:
             pass
 
 
+class HodlrPart:
+    """Part j of a product partitioned at tree level g (hodlr_part_*): the
+    rows of node (g, j).  ``partial(X_j, yred)`` fills ``yred`` (the levels
+    1..g of V^T X over the part's rows); the caller sums ``yred`` over the
+    2^g parts (e.g. ``torch.distributed.all_reduce``); ``finish(X_j, yred)``
+    returns the part's rows of H X.  Keeps the matrix alive."""
+
+    def __init__(self, matrix: "HodlrMatrix", g: int, j: int, nrhs: int):
+        self._m = matrix
+        self.nrhs = int(nrhs)
+        self._p = ctypes.c_void_p()
+        check(load().hodlr_part_create(matrix._h, int(g), int(j), self.nrhs, ctypes.byref(self._p)),
+              "hodlr_part_create")
+        r0, nr, yc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(load().hodlr_part_info(self._p, ctypes.byref(r0), ctypes.byref(nr), ctypes.byref(yc)),
+              "hodlr_part_info")
+        self.row0, self.rows, self.yred_count = r0.value, nr.value, yc.value
+
+    def _x(self, X: torch.Tensor) -> torch.Tensor:
+        if (X.dim() != 2 or X.stride(1) != 1 or X.shape != (self.rows, self.nrhs) or X.dtype != self._m.dtype
+                or not X.is_cuda):
+            raise ValueError("X must be the part's (rows, nrhs) CUDA tensor of the working dtype, unit column stride")
+        return X
+
+    def new_yred(self) -> torch.Tensor:
+        return torch.empty(max(self.yred_count, 1), dtype=self._m.dtype, device="cuda")
+
+    def partial(self, X: torch.Tensor, yred: torch.Tensor, stream=None) -> None:
+        X = self._x(X)
+        if yred.numel() < self.yred_count or yred.dtype != self._m.dtype or not yred.is_contiguous():
+            raise ValueError("yred must hold yred_count contiguous values of the working dtype")
+        check(load().hodlr_part_partial(self._p, X.data_ptr(), X.stride(0), yred.data_ptr(), _stream_ptr(stream)),
+              "hodlr_part_partial")
+
+    def finish(self, X: torch.Tensor, yred: torch.Tensor, B: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        X = self._x(X)
+        if B is None:
+            B = torch.empty_like(X)
+        if B.shape != X.shape or B.stride(1) != 1 or B.dtype != X.dtype or not B.is_cuda:
+            raise ValueError("B must be a (rows, nrhs) CUDA tensor like X")
+        if yred.numel() < self.yred_count or yred.dtype != self._m.dtype or not yred.is_contiguous():
+            raise ValueError("yred must hold yred_count contiguous values of the working dtype")
+        check(load().hodlr_part_finish(self._p, X.data_ptr(), X.stride(0), yred.data_ptr(), B.data_ptr(),
+                                       B.stride(0), _stream_ptr(stream)), "hodlr_part_finish")
+        return B
+
+    def close(self):
+        if self._p:
+            load().hodlr_part_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def dense_kernel_matvec(points: torch.Tensor, kind: int, X: torch.Tensor, c: float = 0.0,
                         len2: float = 1.0, diag: float = 0.0, rows: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:
