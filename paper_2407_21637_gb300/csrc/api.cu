@@ -540,7 +540,7 @@ hodlr_status finish_from_staging(hodlr_s* h, const double* d_stage, const double
       red.poff0 = poff;
       red.yscat0 = yscat0[q];
       red.nyscat = nyscat[q];
-      VChunk ch;
+      VChunk ch{};
       bool open = false;
       auto close_chunk = [&]() {
         if (!open) return;
