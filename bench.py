@@ -878,6 +878,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the FP64 comparison and error checks")
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-threads", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-products block and print its JSON (for profiling runs)")
     ap.add_argument("--c5", action="store_true",
                     help="add the n = 2^20 product block (hodlr_build takes about ten minutes)")
     args = ap.parse_args()
@@ -891,6 +893,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        flush = torch.empty(max(2 * l2, 256 << 20) // 4, dtype=torch.float32, device=dev)
+        peak, _ = _peaks()
+        print(json.dumps(run_batch_block(dev, peak, flush, torch.cuda.current_stream())))
+        return 0
     import torch
     torch.cuda.set_device(local)
     dist = None

@@ -70,6 +70,14 @@ def test_validation_before_device_work(lib):
                                          ctypes.c_void_p(8), 1, ctypes.c_void_p(8), 1, None) == 1
     assert h.value is None
     lib.hodlr_destroy(None)
+    # partitioned product: null handle / part
+    part = ctypes.c_void_p()
+    assert lib.hodlr_part_create(None, 0, 0, 1, ctypes.byref(part)) == 1
+    assert part.value is None
+    assert lib.hodlr_part_partial(None, None, 1, None, None) == 1
+    assert lib.hodlr_part_finish(None, None, 1, None, None, 1, None) == 1
+    assert lib.hodlr_part_info(None, None, None, None) == 1
+    lib.hodlr_part_destroy(None)
 
 
 def test_load_rejects_bad_files_before_device_work(lib, tmp_path):
