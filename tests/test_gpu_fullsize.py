@@ -70,3 +70,37 @@ def test_full_size_sampled_parity(full, R):
     got = B1.cpu().numpy().astype(np.float64)[rows]
     err = np.abs(got - ref)
     assert np.all(err <= tol), float(np.max(err / tol))
+
+
+def test_full_size_partitioned(full):
+    """The row-partitioned product (hodlr_part_*, 8 parts of tree level 3 on
+    separate streams, the levels 1..3 of V^T X summed on the device) at full
+    size: every sampled entry within the same entrywise bound (it holds for
+    any order of the sums)."""
+    from paper_2407_21637_gb300 import HodlrPart
+    h, g, rows = full
+    R = 8
+    X = synth.rhs_normal(h.n, R, 900, np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    parts = [HodlrPart(g, 3, j, R) for j in range(8)]
+    streams = [torch.cuda.Stream() for _ in parts]
+    xs = [Xd[p.row0:p.row0 + p.rows] for p in parts]
+    yreds = [p.new_yred() for p in parts]
+    torch.cuda.synchronize()
+    for p, s, x, y in zip(parts, streams, xs, yreds):
+        p.partial(x, y, stream=s)
+    torch.cuda.synchronize()
+    ysum = torch.stack(yreds).sum(dim=0)
+    Bs = [p.finish(x, ysum, stream=s) for p, s, x in zip(parts, streams, xs)]
+    torch.cuda.synchronize()
+    for p in parts:
+        p.close()
+    B = torch.cat(Bs)
+    assert bool(torch.isfinite(B).all())
+    X64 = X.astype(np.float64)
+    ref = M.hodlr_matvec_rows(h, X64, rows)
+    gabs = M.abs_product_rows(h, X64, rows)
+    u = F.unit_roundoff("fp32")
+    tol = (Bd.gamma(M.max_chain(h), u) + 2 * u) * gabs + u * np.abs(ref)
+    err = np.abs(B.cpu().numpy().astype(np.float64)[rows] - ref)
+    assert np.all(err <= tol), float(np.max(err / tol))
