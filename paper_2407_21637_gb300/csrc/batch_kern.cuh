@@ -144,57 +144,57 @@ __host__ __device__ constexpr int batch_dq() { return RB <= 4 ? 8 : 4; }
 // per row step).
 template <typename W, int RB, bool XV>
 __device__ __forceinline__ void item_vtx_x(const BItem& b, const int w0, const int nw) {
-    const int lane = threadIdx.x & 31;
-    const W* X = reinterpret_cast<const W*>(b.X);
-    W* P = reinterpret_cast<W*>(b.P);
-    const int R = b.R;
-    for (int u = w0; u < b.nunits; u += nw) {
-      const int4 un = b.units[u];
-      const NodeDev& nd = b.nodes[un.x];
-      auto unit = [&](auto tc) {
-        constexpr int TIER = decltype(tc)::value;
-        constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
-        constexpr int CG = batch_cols<W, RB>();
-        for (int c0 = 0; c0 < nd.rV; c0 += CG) {
-          W acc[CG][RB];
+  const int lane = threadIdx.x & 31;
+  const W* X = reinterpret_cast<const W*>(b.X);
+  W* P = reinterpret_cast<W*>(b.P);
+  const int R = b.R;
+  for (int u = w0; u < b.nunits; u += nw) {
+    const int4 un = b.units[u];
+    const NodeDev& nd = b.nodes[un.x];
+    auto unit = [&](auto tc) {
+      constexpr int TIER = decltype(tc)::value;
+      constexpr int eb = TIER == HODLR_FP64 ? 8 : TIER == HODLR_FP32 ? 4 : (TIER == HODLR_E4M3 || TIER == HODLR_E5M2) ? 1 : 2;
+      constexpr int CG = batch_cols<W, RB>();
+      for (int c0 = 0; c0 < nd.rV; c0 += CG) {
+        W acc[CG][RB];
 #pragma unroll
-          for (int a = 0; a < CG; ++a)
+        for (int a = 0; a < CG; ++a)
 #pragma unroll
-            for (int j = 0; j < RB; ++j) acc[a][j] = (W)0;
-          for (int l = un.y; l < un.z; ++l) {
-            const LeafDev& lf = b.leaves[l];
-            const int lm = lf.m, lrow0 = lf.row0;
-            const uint8_t* col0 = b.pool + nd.offV + ((int64_t)c0 * nd.pm + (lf.prow0 - nd.prow0)) * eb;
-            const int64_t cstride = (int64_t)nd.pm * eb;
-            constexpr int kU = batch_unroll<W, RB>();
+          for (int j = 0; j < RB; ++j) acc[a][j] = (W)0;
+        for (int l = un.y; l < un.z; ++l) {
+          const LeafDev& lf = b.leaves[l];
+          const int lm = lf.m, lrow0 = lf.row0;
+          const uint8_t* col0 = b.pool + nd.offV + ((int64_t)c0 * nd.pm + (lf.prow0 - nd.prow0)) * eb;
+          const int64_t cstride = (int64_t)nd.pm * eb;
+          constexpr int kU = batch_unroll<W, RB>();
 #pragma unroll kU
-            for (int r = lane; r < lm; r += 32) {
-              W xv[RB];
-              ld_xrow<W, RB, XV>(X + (lrow0 + r - b.row_base) * b.ldx, R, xv);
+          for (int r = lane; r < lm; r += 32) {
+            W xv[RB];
+            ld_xrow<W, RB, XV>(X + (lrow0 + r - b.row_base) * b.ldx, R, xv);
 #pragma unroll
-              for (int a = 0; a < CG; ++a) {
-                // columns past the rank read the last column (never stored)
-                const int cc = min(a, nd.rV - 1 - c0);
-                const W v = ldg_fmt<W, TIER>(col0 + cc * cstride + (int64_t)r * eb);
+            for (int a = 0; a < CG; ++a) {
+              // columns past the rank read the last column (never stored)
+              const int cc = min(a, nd.rV - 1 - c0);
+              const W v = ldg_fmt<W, TIER>(col0 + cc * cstride + (int64_t)r * eb);
 #pragma unroll
-                for (int j = 0; j < RB; ++j) acc[a][j] = fma(v, xv[j], acc[a][j]);
-              }
-            }
-          }
-#pragma unroll
-          for (int a = 0; a < CG; ++a) {
-            if (c0 + a >= nd.rV) break;
-#pragma unroll
-            for (int j = 0; j < RB; ++j) {
-              if (j >= R) break;
-              const W sm = warp_sum(acc[a][j]);
-              if (lane == 0) P[(int64_t)(un.w + c0 + a) * R + j] = sm;
+              for (int j = 0; j < RB; ++j) acc[a][j] = fma(v, xv[j], acc[a][j]);
             }
           }
         }
-      };
-      with_format(nd.tierV, unit);
-    }
+#pragma unroll
+        for (int a = 0; a < CG; ++a) {
+          if (c0 + a >= nd.rV) break;
+#pragma unroll
+          for (int j = 0; j < RB; ++j) {
+            if (j >= R) break;
+            const W sm = warp_sum(acc[a][j]);
+            if (lane == 0) P[(int64_t)(un.w + c0 + a) * R + j] = sm;
+          }
+        }
+      }
+    };
+    with_format(nd.tierV, unit);
+  }
 }
 // (the X-row load form fixed at compile time: a branch in the unrolled row
 // loop would keep its loads from being issued together)
@@ -210,24 +210,24 @@ __device__ __forceinline__ void item_vtx(const BItem& b, const int w0, const int
 // w0 + nw, ... over the nodes; the summed levels' rows go to Yred.
 template <typename W, int RB>
 __device__ __forceinline__ void item_y(const BItem& b, const int w0, const int nw) {
-    const int lane = threadIdx.x & 31;
-    W* Y = reinterpret_cast<W*>(b.Y);
-    W* Yr = reinterpret_cast<W*>(b.Yred);
-    const W* P = reinterpret_cast<const W*>(b.P);
-    const int R = b.R;
-    for (int q = w0; q < b.nnodes; q += nw) {
-      const NodeDev& nd = b.nodes[q];
-      W* const Yq = (b.yoff[q] < b.yred_rows ? Yr : Y) + (int64_t)b.yoff[q] * RB;
-      const W sc = (W)(nd.invsV * b.nodes[q ^ 1].invsU);
-      const int u0 = b.node_u[q], u1 = b.node_u[q + 1];
-      for (int e2 = lane; e2 < nd.rV * RB; e2 += 32) {
-        const int c = e2 / RB, j = e2 - c * RB;
-        W s = (W)0;
-        if (j < R)
-          for (int u = u0; u < u1; ++u) s += P[(int64_t)(b.units[u].w + c) * R + j];
-        Yq[(int64_t)c * RB + j] = s * sc;   // rows of RB values, zeros past R
-      }
+  const int lane = threadIdx.x & 31;
+  W* Y = reinterpret_cast<W*>(b.Y);
+  W* Yr = reinterpret_cast<W*>(b.Yred);
+  const W* P = reinterpret_cast<const W*>(b.P);
+  const int R = b.R;
+  for (int q = w0; q < b.nnodes; q += nw) {
+    const NodeDev& nd = b.nodes[q];
+    W* const Yq = (b.yoff[q] < b.yred_rows ? Yr : Y) + (int64_t)b.yoff[q] * RB;
+    const W sc = (W)(nd.invsV * b.nodes[q ^ 1].invsU);
+    const int u0 = b.node_u[q], u1 = b.node_u[q + 1];
+    for (int e2 = lane; e2 < nd.rV * RB; e2 += 32) {
+      const int c = e2 / RB, j = e2 - c * RB;
+      W s = (W)0;
+      if (j < R)
+        for (int u = u0; u < u1; ++u) s += P[(int64_t)(b.units[u].w + c) * R + j];
+      Yq[(int64_t)c * RB + j] = s * sc;   // rows of RB values, zeros past R
     }
+  }
 }
 
 // Step 3: B rows = D X + U Y of leaves [lf_lo, lf_hi), warps w0, w0 + nw,
@@ -236,19 +236,19 @@ __device__ __forceinline__ void item_y(const BItem& b, const int w0, const int n
 template <typename W, int RB>
 __device__ __forceinline__ void item_apply(const BItem& b, const int w0, const int nw, const int lf_lo,
                                            const int lf_hi) {
-    constexpr int es = sizeof(W);
-    constexpr int G16 = 16 / es;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const W* X = reinterpret_cast<const W*>(b.X);
-    const W* Y = reinterpret_cast<const W*>(b.Y);
-    const W* Yr = reinterpret_cast<const W*>(b.Yred);
-    const int R = b.R;
-    const bool xvec = b.xvec != 0;
-    W* B = reinterpret_cast<W*>(b.B);
-    extern __shared__ __align__(16) uint8_t bsm[];
-    W* const xs = reinterpret_cast<W*>(bsm + (size_t)warp * kSlice);
-    const uint32_t us = (uint32_t)__cvta_generic_to_shared(bsm + (size_t)warp * kSlice + kXSlice);
-    for (int lf = lf_lo + w0; lf < lf_hi; lf += nw) {
+  constexpr int es = sizeof(W);
+  constexpr int G16 = 16 / es;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const W* X = reinterpret_cast<const W*>(b.X);
+  const W* Y = reinterpret_cast<const W*>(b.Y);
+  const W* Yr = reinterpret_cast<const W*>(b.Yred);
+  const int R = b.R;
+  const bool xvec = b.xvec != 0;
+  W* B = reinterpret_cast<W*>(b.B);
+  extern __shared__ __align__(16) uint8_t bsm[];
+  W* const xs = reinterpret_cast<W*>(bsm + (size_t)warp * kSlice);
+  const uint32_t us = (uint32_t)__cvta_generic_to_shared(bsm + (size_t)warp * kSlice + kXSlice);
+  for (int lf = lf_lo + w0; lf < lf_hi; lf += nw) {
     const int lt0 = b.leaf_t0[lf], lt1 = b.leaf_t0[lf + 1];
     const int lm = b.tiles[lt0].m, lx0 = b.tiles[lt0].xrow0;
     const bool staged = (int64_t)lm * RB * es <= kXSlice;
@@ -381,7 +381,7 @@ __device__ __forceinline__ void item_apply(const BItem& b, const int w0, const i
       }
     }
     __syncwarp();   // the slice is read before the next leaf's rows overwrite it
-    }
+  }
 }
 
 // One matrix's product by the whole CTA (the three steps, CTA barriers
