@@ -440,6 +440,21 @@ hodlr_status hodlr_part_finish(hodlr_part_t p, const void* X, int64_t ldx, const
  * device work).  NULL is a no-op. */
 void hodlr_part_destroy(hodlr_part_t p);
 
+/* hodlr_tree_order -- host function (no device work): the order in which
+ * to pass points in 1 to 3 dimensions so that every node of the cluster tree
+ * (Def. 2.1, ceiling split of Sect. 4) of the given depth is a spatial
+ * cluster -- a kd-tree on the tree's ranges.  Going down the tree, the
+ * points of each node are sorted by the coordinate along which they spread
+ * most (max - min; the lowest such coordinate on a tie), ties by original
+ * index; the node's left child is its first ceil(m/2) positions.  For 1D
+ * points (depth >= 1) this is a stable sort.
+ *  points  host, (n, dim) fp64 row-major, finite; not modified.
+ *  perm    host int32[n], written: perm[t] = the original index of the point
+ *          at tree position t (pass points[perm[t]] to hodlr_build).
+ * Errors: HODLR_EINVAL (n < 1, dim outside 1..3, 2^depth > n, a non-finite
+ * coordinate, NULL arrays); perm is unspecified then. */
+hodlr_status hodlr_tree_order(int32_t n, int32_t dim, const double* points, int32_t depth, int32_t* perm);
+
 /* hodlr_node_sizes -- per node (layout as ranks in hodlr_import: node
  * q = 2^k - 2 + i is (k, i), k = 1..depth) its first row and its rows, the
  * ceil-half cluster tree of Def. 2.1 (the leaves are the level-depth nodes;

@@ -6,4 +6,5 @@ include/hodlr.h); this package only marshals arguments.  PyTorch provides
 device memory and streams.
 """
 from ._lib import PREC, PREC_NAME, HodlrError, load  # noqa: F401
-from .hodlr import HodlrBatch, HodlrMatrix, HodlrPart, RankPredictor, dense_kernel_matvec  # noqa: F401
+from .hodlr import (HodlrBatch, HodlrMatrix, HodlrPart, RankPredictor, dense_kernel_matvec,  # noqa: F401
+                    tree_order)

@@ -95,6 +95,7 @@ SIGNATURES = {
     "hodlr_batch_run": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "hodlr_batch_tune": (ctypes.c_int, [_P, _P, _I32P, ctypes.POINTER(ctypes.c_float)]),
     "hodlr_batch_destroy": (None, [_P]),
+    "hodlr_tree_order": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _I32P]),
     "hodlr_part_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
     "hodlr_part_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64)]),

@@ -514,6 +514,19 @@ class HodlrPart:
             pass
 
 
+def tree_order(points, depth: int) -> np.ndarray:
+    """hodlr_tree_order: the kd-tree order of ``points`` ((n, dim) or (n,)
+    host array) for a cluster tree of the given depth; returns perm (int32)
+    with points[perm] in tree order."""
+    P = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
+    n = P.shape[0]
+    P = P.reshape(n, -1)
+    perm = np.empty(n, dtype=np.int32)
+    check(load().hodlr_tree_order(n, P.shape[1], P.ctypes.data, int(depth),
+                                  perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "hodlr_tree_order")
+    return perm
+
+
 def dense_kernel_matvec(points: torch.Tensor, kind: int, X: torch.Tensor, c: float = 0.0,
                         len2: float = 1.0, diag: float = 0.0, rows: torch.Tensor | None = None,
                         stream=None) -> torch.Tensor:

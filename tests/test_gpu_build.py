@@ -161,3 +161,32 @@ def test_build_oversized_sketch_is_exact(sketch):
             assert U.shape[1] <= 10
             assert np.linalg.norm(U.T @ U - np.eye(U.shape[1])) <= 1e-12
     g.close()
+
+
+def test_build_2d_points_in_kd_order():
+    """The LU workload's kernel, log(r + 1e-4) + n I, on 2D points U[0,1]^2
+    put in kd order by hodlr_tree_order (eps 1e-4, fp64 work): every block
+    meets Def. 2.3 with a rank within +5 of the truncated SVD's, and the
+    product's backward error obeys Thm 3.5."""
+    from paper_2407_21637_gb300 import tree_order
+    n, depth, eps = 1024, 3, 1e-4
+    spec = synth.KernelSpec(K.LOG, c=1e-4, diag=float(n))
+    raw = synth.uniform_points_2d(n, 47)
+    pts = np.ascontiguousarray(raw[tree_order(raw, depth)])
+    A = K.kernel_matrix(pts, spec)
+    g = _gpu_build(pts, spec, depth, eps, "fp64", ("fp64",))
+    h = _as_oracle(g, n, depth)
+    ref = C.compress(pts, spec, n, depth, eps, A=A)
+    for k in range(1, depth + 1):
+        for i, (s, m) in enumerate(h.levels[k]):
+            (s1, m1) = h.levels[k][i ^ 1]
+            blk = A[s:s + m, s1:s1 + m1]
+            err = np.linalg.norm(blk - h.U[k][i] @ h.V[k][i ^ 1].T)
+            assert err <= eps * np.linalg.norm(blk) * (1 + 1e-6), (k, i)
+            r, r_opt = h.U[k][i].shape[1], ref.rank(k, i)
+            assert r_opt <= r <= r_opt + 5, (k, i, r, r_opt)
+    x = synth.rhs_normal(n, 1, 11, np.float64)[:, 0]
+    b = g.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert F.unit_roundoff("fp64") <= eps / n
+    assert np.linalg.norm(b - A @ x) / (np.linalg.norm(A) * np.linalg.norm(x)) <= Bd.matvec_backward_bound(eps, depth)
+    g.close()
